@@ -1,0 +1,241 @@
+/*
+ * lbm.h -- C interface of the GB300 library for the lattice Boltzmann method
+ * with fully resolved moving rigid particles (Bartuschat, Fischermeier,
+ * Gustavsson, Ruede, "Two computational models for simulating the tumbling
+ * motion of elongated particles in fluids", Sec. 4).
+ *
+ * The problem the interface states (Sec. 4.2-4.3): a box of fluid on a
+ * Cartesian lattice, with periodic or moving-wall boundaries, holding rigid
+ * bodies mapped onto the lattice as obstacle cells; fluid and bodies advance
+ * together, two-way coupled, and the hydrodynamic force and torque on every
+ * body and the fluid fields can be read back.
+ *
+ * Conventions
+ *  - Lattice units throughout: dx = dt = 1.  Cell (i,j,k) has centre (i,j,k)
+ *    and linear index idx = i + nx*(j + ny*k) (x fastest).
+ *  - D3Q19 velocities (Sec. 4.1, weights 1/3, 1/18, 1/36), numbered
+ *      0: (0,0,0)
+ *      1..6: +x, -x, +y, -y, +z, -z
+ *      7..18: (1,1,0),(-1,-1,0),(1,-1,0),(-1,1,0),(1,0,1),(-1,0,-1),
+ *             (1,0,-1),(-1,0,1),(0,1,1),(0,-1,-1),(0,1,-1),(0,-1,1)
+ *    so that the opposite of q > 0 is the other member of its pair.
+ *  - Canonical populations ("pdfs") are the post-stream values f_q(x) at the
+ *    start of the next collision, stored as double f[q*n + idx], n = nx*ny*nz.
+ *    Non-fluid cells report 0 for populations, density and velocity.
+ *  - Every call returns an lbm_status; 0 is success.  No exception crosses the
+ *    interface.  lbm_last_error() gives a message for the last failure.
+ *  - The caller owns every host buffer passed in; the library never keeps or
+ *    frees caller memory.  Device memory is taken from the caller's allocator
+ *    callbacks when given, otherwise from cudaMalloc, and is released by
+ *    lbm_destroy.
+ *  - Work is ordered on the stream given at creation.  lbm_step is
+ *    asynchronous; calls that return host data synchronise that stream.
+ *  - A context is used by one host thread at a time.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_Q 19
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum lbm_status {
+    LBM_OK = 0,
+    LBM_ERR_ARG = 1,         /* invalid argument (sizes, tau <= 1/2, NULL ...) */
+    LBM_ERR_STATE = 2,       /* call not valid in the context's state */
+    LBM_ERR_OOM = 3,         /* device allocation failed */
+    LBM_ERR_CUDA = 4,        /* a CUDA runtime call failed */
+    LBM_ERR_NUMERIC = 5,     /* non-finite force or particle state detected */
+    LBM_ERR_TIMEOUT = 6,     /* a bounded device-side wait ran out */
+    LBM_ERR_UNSUPPORTED = 7  /* request outside what this build supports */
+} lbm_status;
+
+/* How populations are stored in device memory.  Every form stores the offset
+ * g_q = f_q - w_q*rho0 from the rest state.  F64 computes in double; the others
+ * compute in float.  Force/torque sums and the rigid-body update are always
+ * double. */
+typedef enum lbm_precision {
+    LBM_F64 = 0,
+    LBM_F32 = 1,
+    LBM_F16_OFFSET = 2,   /* IEEE binary16 offsets, round to nearest even */
+    LBM_BF16_OFFSET = 3   /* bfloat16 offsets, round to nearest even */
+} lbm_precision;
+
+/* Particle-id map codes of cells that are not particle cells. */
+#define LBM_PID_FLUID    0xFFFFFFFFu
+#define LBM_PID_WALL_YLO 0xFFFFFFFEu  /* wall layer y = 0, moves at wall_u_lo */
+#define LBM_PID_WALL_YHI 0xFFFFFFFDu  /* wall layer y = ny-1, moves at wall_u_hi */
+#define LBM_PID_WALL     0xFFFFFFFCu  /* resting wall layer of a non-periodic x or z face */
+
+/* Canonical cell flags returned by lbm_get_fields. */
+#define LBM_FLAG_FLUID    0
+#define LBM_FLAG_WALL     1
+#define LBM_FLAG_PARTICLE 2
+
+/* One lattice (Sec. 4.1).  A non-periodic axis is closed by one layer of wall
+ * cells on each side: the y layers move with wall_u_lo / wall_u_hi (velocity
+ * bounce-back, Eq. LBMMovWall), x and z layers rest (Eq. BBBC).  With the TRT
+ * "magic" product Lambda = (tau - 1/2)(tau_odd - 1/2) = 3/16 the walls sit half-way
+ * between cells (Sec. 4.1).  body_force is a constant force density on the
+ * fluid, entered as the odd source 3 w_q rho0 c_q.g after collision. */
+typedef struct lbm_grid_desc {
+    int nx, ny, nz;            /* >= 3 each */
+    double tau;                /* > 1/2; viscosity (tau - 1/2)/3 (Eq. kinVisc) */
+    double magic;              /* TRT Lambda > 0; 3/16 in all of Sec. 5-6 */
+    double rho0;               /* mean density, > 0 (usually 1) */
+    int periodic[3];           /* 1 = periodic along x, y, z */
+    double wall_u_lo[3];       /* velocity of the y = 0 wall layer, |u| < 0.1 */
+    double wall_u_hi[3];       /* velocity of the y = ny-1 wall layer, |u| < 0.1 */
+    double body_force[3];      /* fluid body-force density */
+    lbm_precision prec;        /* storage form (same for every cell of a batch) */
+    void *cuda_stream;         /* cudaStream_t for all work; NULL = legacy default stream */
+    void *(*dev_alloc)(size_t bytes, void *user); /* optional device allocator */
+    void (*dev_free)(void *ptr, void *user);       /* its matching free */
+    void *user;                /* passed to dev_alloc / dev_free */
+} lbm_grid_desc;
+
+/* One rigid ellipsoid (Sec. 4.2-4.3).  Semi-axes are along the body x, y, z
+ * axes; quat = (w, x, y, z) rotates body to world coordinates and is
+ * normalised by the library.  Mass = density * 4/3 pi a b c (density relative
+ * to rho0 = 1 units), inertia of the solid ellipsoid.  ext_force and
+ * ext_torque are added to the hydrodynamic force and torque every step.  A
+ * fixed body keeps its pose and velocities.  cell selects the lattice of a
+ * batch (0 for a single lattice). */
+typedef struct lbm_particle {
+    double pos[3];
+    double quat[4];
+    double vel[3];
+    double omega[3];
+    double semi_axes[3];
+    double density;
+    double ext_force[3];
+    double ext_torque[3];
+    int cell;
+    int fixed;
+} lbm_particle;
+
+/* Create one lattice, fluid at rest with density rho0 (f_q = w_q rho0).
+ * Errors: LBM_ERR_ARG for a NULL pointer, a size < 3, tau <= 1/2, magic <= 0,
+ * rho0 <= 0, a wall speed component >= 0.1 in magnitude, an unknown precision,
+ * or a lattice above 2^31 cells; LBM_ERR_OOM; LBM_ERR_CUDA. */
+lbm_status lbm_create(const lbm_grid_desc *desc, lbm_ctx **out);
+
+/* Create a batch of independent lattices advanced together (one sweep launch
+ * per step over all of them).  prec, cuda_stream and the allocator are taken
+ * from cells[0] and must be the same in every entry.  Errors as lbm_create. */
+lbm_status lbm_create_batch(const lbm_grid_desc *cells, int ncells, lbm_ctx **out);
+
+/* Replace the particle set and re-map the obstacle cells from the given poses
+ * (Sec. 4.2: a non-wall cell is an obstacle cell of a body iff its centre lies
+ * inside it; a cell inside several bodies belongs to the lowest index).
+ * Particle cells that become fluid are refilled with f^eq(rho0, 0); cells that
+ * become obstacles drop their populations.  n = 0 removes all particles.
+ * Errors: LBM_ERR_ARG for n < 0, p == NULL with n > 0, a cell index out of
+ * range, semi-axes <= 0, density <= 0, or a body not inside the fluid region
+ * of a non-periodic axis. */
+lbm_status lbm_set_particles(lbm_ctx *ctx, const lbm_particle *p, int n);
+
+/* Advance nsteps time steps, asynchronously on the context's stream.  One step
+ * (Sec. 4.1-4.3): the fused stream-collide sweep over every fluid cell with
+ * velocity bounce-back at walls and obstacle cells and the momentum-exchange
+ * force/torque sums (Eqs. LBMCollide, LBMStream, LBMMovWall,
+ * LBMhydrodynForce); the rigid-body update; the re-mapping of obstacle cells
+ * with equilibrium refill of uncovered cells (Sec. 4.2).
+ * Errors: LBM_ERR_ARG for nsteps < 0; LBM_ERR_STATE after an earlier
+ * numeric error; LBM_ERR_CUDA. */
+lbm_status lbm_step(lbm_ctx *ctx, int nsteps);
+
+/* Wait for all queued work; reports LBM_ERR_NUMERIC if a non-finite force was
+ * met since the last check. */
+lbm_status lbm_sync(lbm_ctx *ctx);
+
+/* Hydrodynamic force and torque (Eq. LBMhydrodynForce; torque about the
+ * centre of mass with lever arm x_s - x_C) of the last completed step, for the
+ * first n particles, as force3n[3*i + a], torque3n[3*i + a].  External loads
+ * are not included.  Synchronises.  Either pointer may be NULL. */
+lbm_status lbm_get_forces(lbm_ctx *ctx, double *force3n, double *torque3n, int n);
+
+/* Momentum handed per step to the y = 0 and y = ny-1 wall layers of lattice
+ * `cell` in the last step: f6[0..2] low wall, f6[3..5] high wall. */
+lbm_status lbm_get_wall_forces(lbm_ctx *ctx, int cell, double *f6);
+
+/* Current particle states (pose, velocities) of the first n particles. */
+lbm_status lbm_get_particles(lbm_ctx *ctx, lbm_particle *p, int n);
+
+/* Set external force/torque of the first n particles (host arrays of 3n
+ * doubles; either may be NULL to leave that part unchanged).  Asynchronous
+ * host-to-device copy on the context's stream; the arrays may be reused
+ * as soon as the call returns. */
+lbm_status lbm_set_external(lbm_ctx *ctx, const double *force3n, const double *torque3n, int n);
+
+/* Fields of lattice `cell` in canonical form (see Conventions): density
+ * rho[n], velocity u3[3*n] (component-major, u = sum(c f)/rho0 + g/2),
+ * flags[n] (LBM_FLAG_*), particle ids pid[n] (LBM_PID_* or the particle
+ * index), populations pdfs[19*n].  Any pointer may be NULL.  Synchronises. */
+lbm_status lbm_get_fields(lbm_ctx *ctx, int cell, double *rho, double *u3, uint8_t *flags,
+                          uint32_t *pid, double *pdfs);
+
+/* Overwrite the populations of the fluid cells of lattice `cell` from a
+ * canonical host array pdfs[19*n] (checkpoint restore, test set-up). */
+lbm_status lbm_set_pdfs(lbm_ctx *ctx, int cell, const double *pdfs);
+
+/* Boundary links {(x_F, q): x_F fluid, x_F + c_q a wall or obstacle cell} of
+ * lattice `cell`, ordered by cell index then q (the direction sets D_s of
+ * Eq. LBMhydrodynForce, walls included), with the id of the cell hit.  Writes
+ * at most cap entries; *count receives the total.  Any output array may be
+ * NULL when cap = 0. */
+lbm_status lbm_get_links(lbm_ctx *ctx, int cell, int32_t *idx, int8_t *q, uint32_t *pid, int cap,
+                         int *count);
+
+typedef struct lbm_info {
+    long long ncells_total;     /* cells over all lattices */
+    long long nfluid_hint;      /* not computed: -1 */
+    int nlattices;
+    int nparticles;
+    long long steps_done;
+    size_t device_bytes;        /* device memory held by the context */
+    int sweep_grid, sweep_block;/* launch shape of the sweep kernel */
+    int bytes_per_population;   /* 8, 4 or 2 */
+} lbm_info;
+
+lbm_status lbm_get_info(lbm_ctx *ctx, lbm_info *info);
+
+/* Sweep launch shape: block threads (multiple of 32, <= 1024) and grid blocks
+ * (<= 0 selects the default: enough resident blocks for every SM).  Used by
+ * the autotuner; takes effect at the next lbm_step. */
+lbm_status lbm_set_launch(lbm_ctx *ctx, int block, int grid);
+
+/* Choose the sweep launch shape by timing candidates on this context (runs
+ * sweeps on scratch copies: the state is restored afterwards).  The chosen
+ * shape is kept and returned through block/grid (either may be NULL). */
+lbm_status lbm_autotune(lbm_ctx *ctx, int *block, int *grid);
+
+/* CUDA graphs: when enabled, lbm_step replays a captured two-step graph for
+ * pairs of steps (default on). */
+lbm_status lbm_set_graphs(lbm_ctx *ctx, int enable);
+
+/* Sweep-kernel timing: when enabled, every sweep launch is bracketed by CUDA
+ * events on the context's stream; lbm_get_sweep_timing returns the summed
+ * device time in milliseconds and the number of launches since enabling
+ * (synchronises) and resets the tally.  Enabling turns graph replay off. */
+lbm_status lbm_set_sweep_timing(lbm_ctx *ctx, int enable);
+lbm_status lbm_get_sweep_timing(lbm_ctx *ctx, double *ms, long long *launches);
+
+/* Number of kernel launches issued by the library since creation. */
+lbm_status lbm_get_launch_count(lbm_ctx *ctx, long long *launches);
+
+lbm_status lbm_destroy(lbm_ctx *ctx);
+const char *lbm_last_error(const lbm_ctx *ctx);
+const char *lbm_status_string(lbm_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

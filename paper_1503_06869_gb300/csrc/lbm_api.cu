@@ -1,0 +1,914 @@
+// lbm_api.cu -- the C interface declared in include/lbm.h: contexts, device
+// memory, the order of the kernels in a time step (Sec. 4.3: sweep with
+// bounce-back and momentum exchange, rigid-body update, re-mapping), CUDA
+// graph replay, sweep timing and the launch-shape autotuner.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lbm_internal.cuh"
+
+using namespace lbm;
+
+struct lbm_ctx {
+    lbm_precision prec = LBM_F32;
+    int esize = 4;
+    cudaStream_t stream = nullptr;
+    void *(*dev_alloc)(size_t, void *) = nullptr;
+    void (*dev_free)(void *, void *) = nullptr;
+    void *user = nullptr;
+    std::vector<void *> owned;      // every device allocation of the context
+    size_t device_bytes = 0;
+
+    int nlat = 0;
+    std::vector<LatDev> lat_h;
+    LatDev *lat_d = nullptr;
+    long long ncells = 0, f_elems = 0;
+    void *f = nullptr;
+    uint8_t *flags = nullptr;
+    uint32_t *pid = nullptr, *pid_prev = nullptr;
+    double *wall_acc = nullptr, *wall_last = nullptr;
+    uint32_t *err = nullptr;
+
+    int np = 0;
+    PartDev P{};
+    std::vector<void *> part_bufs;
+
+    long long t = 0;
+    int block = 256, grid = 0, ntiles = 0;
+    int remap_bpb = 8;
+
+    bool graphs = true;
+    cudaGraphExec_t gexec = nullptr;
+    bool gvalid = false;
+
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;
+    size_t ev_used = 0;
+    double ms_acc = 0.0;
+    long long timed_launches = 0;
+
+    long long launches = 0;
+    bool broken = false;
+    std::string msg;
+};
+
+namespace {
+
+lbm_status fail(lbm_ctx *c, lbm_status s, const std::string &m) {
+    if (c) c->msg = m;
+    return s;
+}
+
+#define CK(call)                                                                         \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(ctx, LBM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+void *dalloc(lbm_ctx *ctx, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void *p = nullptr;
+    if (ctx->dev_alloc) {
+        p = ctx->dev_alloc(bytes, ctx->user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    return p;
+}
+
+void dfree(lbm_ctx *ctx, void *p) {
+    if (!p) return;
+    if (ctx->dev_free)
+        ctx->dev_free(p, ctx->user);
+    else
+        cudaFree(p);
+}
+
+void *owned_alloc(lbm_ctx *ctx, size_t bytes) {
+    void *p = dalloc(ctx, bytes);
+    if (p) {
+        ctx->owned.push_back(p);
+        ctx->device_bytes += bytes;
+    }
+    return p;
+}
+
+int storage_bytes(lbm_precision p) {
+    switch (p) {
+    case LBM_F64: return 8;
+    case LBM_F32: return 4;
+    case LBM_F16_OFFSET:
+    case LBM_BF16_OFFSET: return 2;
+    }
+    return 0;
+}
+
+lbm_status check_desc(const lbm_grid_desc *d, std::string &m) {
+    if (d->nx < 3 || d->ny < 3 || d->nz < 3) { m = "lattice sizes must be >= 3"; return LBM_ERR_ARG; }
+    if ((long long)d->nx * d->ny * d->nz > 0x7FFFFFFFll) { m = "lattice above 2^31 cells"; return LBM_ERR_ARG; }
+    if (!(d->tau > 0.5) || !std::isfinite(d->tau)) { m = "tau must be > 1/2"; return LBM_ERR_ARG; }
+    if (!(d->magic > 0.0) || !std::isfinite(d->magic)) { m = "magic must be > 0"; return LBM_ERR_ARG; }
+    if (!(d->rho0 > 0.0) || !std::isfinite(d->rho0)) { m = "rho0 must be > 0"; return LBM_ERR_ARG; }
+    for (int a = 0; a < 3; ++a) {
+        if (!(std::fabs(d->wall_u_lo[a]) < 0.1) || !(std::fabs(d->wall_u_hi[a]) < 0.1)) {
+            m = "wall speed components must be below 0.1 (Mach limit)";
+            return LBM_ERR_ARG;
+        }
+        if (!std::isfinite(d->body_force[a])) { m = "body force must be finite"; return LBM_ERR_ARG; }
+    }
+    if (storage_bytes(d->prec) == 0) { m = "unknown precision"; return LBM_ERR_ARG; }
+    return LBM_OK;
+}
+
+void fill_tiles(lbm_ctx *ctx) {
+    int tile = 0;
+    for (auto &L : ctx->lat_h) {
+        L.tile0 = tile;
+        tile += (L.n + ctx->block - 1) / ctx->block;
+    }
+    ctx->ntiles = tile;
+}
+
+int default_grid(lbm_ctx *ctx) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int nb = sweep_max_active_blocks(ctx->prec, 1, ctx->block);
+    if (nb <= 0) nb = 1;
+    long long g = (long long)sms * nb;
+    if (g > ctx->ntiles) g = ctx->ntiles;
+    return (int)(g > 0 ? g : 1);
+}
+
+SweepArgs sweep_args(lbm_ctx *ctx) {
+    SweepArgs a;
+    a.lat0 = ctx->lat_h[0];
+    a.lat = ctx->lat_d;
+    a.nlat = ctx->nlat;
+    a.ntiles = ctx->ntiles;
+    a.f = ctx->f;
+    a.flags = ctx->flags;
+    a.pid = ctx->pid;
+    a.P = ctx->P;
+    a.wall_acc = ctx->wall_acc;
+    a.err = ctx->err;
+    return a;
+}
+
+RemapArgs remap_args(lbm_ctx *ctx) {
+    RemapArgs a;
+    a.lat = ctx->lat_d;
+    a.f = ctx->f;
+    a.flags = ctx->flags;
+    a.pid = ctx->pid;
+    a.pid_prev = ctx->pid_prev;
+    a.P = ctx->P;
+    a.wall_acc = ctx->wall_acc;
+    a.wall_last = ctx->wall_last;
+    a.nlat = ctx->nlat;
+    a.err = ctx->err;
+    return a;
+}
+
+lbm_status upload_lattices(lbm_ctx *ctx) {
+    CK(cudaMemcpyAsync(ctx->lat_d, ctx->lat_h.data(), sizeof(LatDev) * ctx->nlat, cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+}
+
+void drop_graph(lbm_ctx *ctx) {
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    ctx->gexec = nullptr;
+    ctx->gvalid = false;
+}
+
+// One time step (Sec. 4.3): sweep at the parity of step t, rigid-body
+// update, re-mapping for the parity of the next sweep.
+lbm_status enqueue_step(lbm_ctx *ctx, bool timed) {
+    const int parity = (int)(ctx->t & 1);
+    SweepArgs sa = sweep_args(ctx);
+    if (timed) {
+        if (ctx->ev_used + 2 > ctx->ev.size()) {
+            for (int i = 0; i < 64; ++i) {
+                cudaEvent_t e;
+                CK(cudaEventCreate(&e));
+                ctx->ev.push_back(e);
+            }
+        }
+        CK(cudaEventRecord(ctx->ev[ctx->ev_used], ctx->stream));
+    }
+    CK(launch_sweep(ctx->prec, parity, sa, ctx->grid, ctx->block, ctx->stream));
+    if (timed) {
+        CK(cudaEventRecord(ctx->ev[ctx->ev_used + 1], ctx->stream));
+        ctx->ev_used += 2;
+        ctx->timed_launches += 1;
+    }
+    RemapArgs ra = remap_args(ctx);
+    CK(launch_rigid_body(ra, ctx->stream));
+    ctx->launches += 2;
+    if (ctx->np > 0) {
+        CK(launch_remap_step(ctx->prec, 1 - parity, ra, ctx->remap_bpb, ctx->stream));
+        ctx->launches += kernels_per_remap_step();
+    }
+    ctx->t += 1;
+    return LBM_OK;
+}
+
+lbm_status harvest_timing(lbm_ctx *ctx) {
+    if (ctx->ev_used == 0) return LBM_OK;
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (size_t i = 0; i + 1 < ctx->ev_used; i += 2) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]));
+        ctx->ms_acc += ms;
+    }
+    ctx->ev_used = 0;
+    return LBM_OK;
+}
+
+lbm_status build_graph(lbm_ctx *ctx) {
+    drop_graph(ctx);
+    cudaGraph_t g = nullptr;
+    const long long t0 = ctx->t, l0 = ctx->launches;
+    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    lbm_status s1 = enqueue_step(ctx, false);
+    lbm_status s2 = s1 == LBM_OK ? enqueue_step(ctx, false) : s1;
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+    ctx->t = t0;
+    ctx->launches = l0;
+    if (s2 != LBM_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s2;
+    }
+    if (e != cudaSuccess) return fail(ctx, LBM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&ctx->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        ctx->gexec = nullptr;
+        return fail(ctx, LBM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    ctx->gvalid = true;
+    return LBM_OK;
+}
+
+lbm_status check_err_word(lbm_ctx *ctx) {
+    uint32_t e = 0;
+    CK(cudaMemcpyAsync(&e, ctx->err, sizeof(e), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (e & ERR_NONFINITE) {
+        ctx->broken = true;
+        return fail(ctx, LBM_ERR_NUMERIC, "non-finite force, torque or particle state");
+    }
+    if (e & ERR_TIMEOUT) {
+        ctx->broken = true;
+        return fail(ctx, LBM_ERR_TIMEOUT, "device-side wait ran out");
+    }
+    return LBM_OK;
+}
+
+void free_particles(lbm_ctx *ctx) {
+    for (void *p : ctx->part_bufs) {
+        for (size_t i = 0; i < ctx->owned.size(); ++i)
+            if (ctx->owned[i] == p) {
+                ctx->owned.erase(ctx->owned.begin() + i);
+                break;
+            }
+        dfree(ctx, p);
+    }
+    ctx->part_bufs.clear();
+    ctx->P = PartDev{};
+    ctx->np = 0;
+}
+
+template <class T>
+T *part_alloc(lbm_ctx *ctx, size_t count) {
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = 16;
+    void *p = dalloc(ctx, bytes);
+    if (p) {
+        ctx->part_bufs.push_back(p);
+        ctx->owned.push_back(p);
+    }
+    return static_cast<T *>(p);
+}
+
+// Row-major rotation matrix of a unit quaternion (w,x,y,z); the same
+// arithmetic order as the device mapping.
+void quat_matrix_host(const double *q, double R[9]) {
+    const double w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0] = 1.0 - 2.0 * (y * y + z * z);
+    R[1] = 2.0 * (x * y - w * z);
+    R[2] = 2.0 * (x * z + w * y);
+    R[3] = 2.0 * (x * y + w * z);
+    R[4] = 1.0 - 2.0 * (x * x + z * z);
+    R[5] = 2.0 * (y * z - w * x);
+    R[6] = 2.0 * (x * z - w * y);
+    R[7] = 2.0 * (y * z + w * x);
+    R[8] = 1.0 - 2.0 * (x * x + y * y);
+}
+
+lbm_status create_common(const lbm_grid_desc *cells, int ncells, lbm_ctx **out) {
+    if (!out) return LBM_ERR_ARG;
+    *out = nullptr;
+    if (!cells || ncells <= 0) return LBM_ERR_ARG;
+    std::string m;
+    for (int i = 0; i < ncells; ++i) {
+        lbm_status s = check_desc(&cells[i], m);
+        if (s != LBM_OK) return s;
+        if (cells[i].prec != cells[0].prec || cells[i].cuda_stream != cells[0].cuda_stream ||
+            cells[i].dev_alloc != cells[0].dev_alloc || cells[i].dev_free != cells[0].dev_free)
+            return LBM_ERR_ARG;
+    }
+    if ((cells[0].dev_alloc == nullptr) != (cells[0].dev_free == nullptr)) return LBM_ERR_ARG;
+    lbm_ctx *ctx = new lbm_ctx();
+    ctx->prec = cells[0].prec;
+    ctx->esize = storage_bytes(ctx->prec);
+    ctx->stream = (cudaStream_t)cells[0].cuda_stream;
+    ctx->dev_alloc = cells[0].dev_alloc;
+    ctx->dev_free = cells[0].dev_free;
+    ctx->user = cells[0].user;
+    ctx->graphs = ctx->stream != nullptr;
+    ctx->nlat = ncells;
+    ctx->lat_h.resize(ncells);
+    long long foff = 0, coff = 0;
+    for (int i = 0; i < ncells; ++i) {
+        const lbm_grid_desc &d = cells[i];
+        LatDev &L = ctx->lat_h[i];
+        memset(&L, 0, sizeof(L));
+        L.nx = d.nx;
+        L.ny = d.ny;
+        L.nz = d.nz;
+        L.n = d.nx * d.ny * d.nz;
+        L.npad = (L.n + 63) / 64 * 64;  // 256-byte aligned planes in every precision
+        L.f_off = foff;
+        L.c_off = coff;
+        L.divx.init((uint32_t)d.nx);
+        L.divxy.init((uint32_t)(d.nx * d.ny));
+        L.px = d.periodic[0] ? 1 : 0;
+        L.py = d.periodic[1] ? 1 : 0;
+        L.pz = d.periodic[2] ? 1 : 0;
+        L.omega = 1.0 / d.tau;
+        L.omega_odd = 1.0 / (d.magic / (d.tau - 0.5) + 0.5);
+        L.rho0 = d.rho0;
+        for (int a = 0; a < 3; ++a) {
+            L.wlo[a] = d.wall_u_lo[a];
+            L.whi[a] = d.wall_u_hi[a];
+            L.g[a] = d.body_force[a];
+        }
+        foff += (long long)Q * L.npad;
+        coff += (L.n + 255) / 256 * 256;
+    }
+    ctx->f_elems = foff;
+    ctx->ncells = coff;
+    fill_tiles(ctx);
+
+    ctx->lat_d = (LatDev *)owned_alloc(ctx, sizeof(LatDev) * ncells);
+    ctx->f = owned_alloc(ctx, (size_t)foff * ctx->esize);
+    ctx->flags = (uint8_t *)owned_alloc(ctx, (size_t)coff);
+    ctx->pid = (uint32_t *)owned_alloc(ctx, (size_t)coff * 4);
+    ctx->pid_prev = (uint32_t *)owned_alloc(ctx, (size_t)coff * 4);
+    ctx->wall_acc = (double *)owned_alloc(ctx, sizeof(double) * 6 * ncells);
+    ctx->wall_last = (double *)owned_alloc(ctx, sizeof(double) * 6 * ncells);
+    ctx->err = (uint32_t *)owned_alloc(ctx, 16);
+    if (!ctx->lat_d || !ctx->f || !ctx->flags || !ctx->pid || !ctx->pid_prev || !ctx->wall_acc ||
+        !ctx->wall_last || !ctx->err) {
+        lbm_destroy(ctx);
+        return LBM_ERR_OOM;
+    }
+    lbm_status s = upload_lattices(ctx);
+    if (s != LBM_OK) {
+        lbm_destroy(ctx);
+        return s;
+    }
+    // fluid at rest: every stored offset f - w rho0 is zero
+    if (cudaMemsetAsync(ctx->f, 0, (size_t)foff * ctx->esize, ctx->stream) != cudaSuccess ||
+        cudaMemsetAsync(ctx->flags, 0, (size_t)coff, ctx->stream) != cudaSuccess ||
+        cudaMemsetAsync(ctx->pid, 0xFF, (size_t)coff * 4, ctx->stream) != cudaSuccess ||
+        cudaMemsetAsync(ctx->wall_acc, 0, sizeof(double) * 6 * ncells, ctx->stream) != cudaSuccess ||
+        cudaMemsetAsync(ctx->wall_last, 0, sizeof(double) * 6 * ncells, ctx->stream) != cudaSuccess ||
+        cudaMemsetAsync(ctx->err, 0, 16, ctx->stream) != cudaSuccess) {
+        lbm_destroy(ctx);
+        return LBM_ERR_CUDA;
+    }
+    for (int i = 0; i < ncells; ++i) {
+        if (launch_init_cells(ctx->lat_h[i], ctx->lat_d + i, ctx->flags, ctx->pid, ctx->pid_prev,
+                              ctx->stream) != cudaSuccess) {
+            lbm_destroy(ctx);
+            return LBM_ERR_CUDA;
+        }
+        ctx->launches += 2;
+    }
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        lbm_destroy(ctx);
+        return LBM_ERR_CUDA;
+    }
+    ctx->grid = default_grid(ctx);
+    *out = ctx;
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_create(const lbm_grid_desc *desc, lbm_ctx **out) { return create_common(desc, 1, out); }
+
+lbm_status lbm_create_batch(const lbm_grid_desc *cells, int ncells, lbm_ctx **out) {
+    return create_common(cells, ncells, out);
+}
+
+lbm_status lbm_destroy(lbm_ctx *ctx) {
+    if (!ctx) return LBM_ERR_ARG;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    drop_graph(ctx);
+    for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+    for (void *p : ctx->owned) dfree(ctx, p);
+    delete ctx;
+    return LBM_OK;
+}
+
+const char *lbm_last_error(const lbm_ctx *ctx) { return ctx ? ctx->msg.c_str() : "null context"; }
+
+const char *lbm_status_string(lbm_status s) {
+    switch (s) {
+    case LBM_OK: return "ok";
+    case LBM_ERR_ARG: return "invalid argument";
+    case LBM_ERR_STATE: return "invalid state";
+    case LBM_ERR_OOM: return "out of device memory";
+    case LBM_ERR_CUDA: return "CUDA error";
+    case LBM_ERR_NUMERIC: return "non-finite value";
+    case LBM_ERR_TIMEOUT: return "device wait timed out";
+    case LBM_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+lbm_status lbm_set_particles(lbm_ctx *ctx, const lbm_particle *p, int n) {
+    if (!ctx) return LBM_ERR_ARG;
+    if (n < 0 || (n > 0 && !p)) return fail(ctx, LBM_ERR_ARG, "bad particle array");
+    // validate and derive host-side quantities
+    std::vector<double> pos(3 * n), quat(4 * n), vel(3 * n), om(3 * n), L(3 * n), semi(3 * n), mass(n),
+        inertia(3 * n), extF(3 * n), extM(3 * n);
+    std::vector<int> cell(n), fixed(n), region(6 * n);
+    for (int i = 0; i < n; ++i) {
+        const lbm_particle &b = p[i];
+        if (b.cell < 0 || b.cell >= ctx->nlat) return fail(ctx, LBM_ERR_ARG, "particle cell index out of range");
+        if (!(b.semi_axes[0] > 0 && b.semi_axes[1] > 0 && b.semi_axes[2] > 0))
+            return fail(ctx, LBM_ERR_ARG, "semi-axes must be positive");
+        if (!(b.density > 0)) return fail(ctx, LBM_ERR_ARG, "density must be positive");
+        double q[4] = {b.quat[0], b.quat[1], b.quat[2], b.quat[3]};
+        const double nrm = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        if (!(nrm > 0) || !std::isfinite(nrm)) return fail(ctx, LBM_ERR_ARG, "quaternion must be non-zero");
+        for (int k = 0; k < 4; ++k) q[k] /= nrm;
+        const LatDev &Lt = ctx->lat_h[b.cell];
+        double R[9];
+        quat_matrix_host(q, R);
+        const int dims[3] = {Lt.nx, Lt.ny, Lt.nz}, per[3] = {Lt.px, Lt.py, Lt.pz};
+        for (int a = 0; a < 3; ++a) {
+            if (!std::isfinite(b.pos[a]) || !std::isfinite(b.vel[a]) || !std::isfinite(b.omega[a]))
+                return fail(ctx, LBM_ERR_ARG, "non-finite particle state");
+            const double e0 = R[3 * a] * b.semi_axes[0], e1 = R[3 * a + 1] * b.semi_axes[1],
+                         e2 = R[3 * a + 2] * b.semi_axes[2];
+            const double h = std::sqrt(e0 * e0 + e1 * e1 + e2 * e2);
+            if (!per[a] && (b.pos[a] - h < 1.0 || b.pos[a] + h > dims[a] - 2.0))
+                return fail(ctx, LBM_ERR_ARG, "particle not inside the fluid region");
+            if (per[a] && !(b.pos[a] >= 0.0 && b.pos[a] < dims[a]))
+                return fail(ctx, LBM_ERR_ARG, "periodic coordinate outside [0, n)");
+            int lo = (int)std::floor(b.pos[a] - h) - 2, hi = (int)std::ceil(b.pos[a] + h) + 2;
+            if (per[a]) {
+                if (hi - lo + 1 > dims[a]) { lo = 0; hi = dims[a] - 1; }
+            } else {
+                lo = lo < 0 ? 0 : lo;
+                hi = hi > dims[a] - 1 ? dims[a] - 1 : hi;
+            }
+            region[6 * i + a] = lo;
+            region[6 * i + 3 + a] = hi - lo + 1;
+        }
+        const double A = b.semi_axes[0], B = b.semi_axes[1], Cc = b.semi_axes[2];
+        const double m = b.density * (4.0 / 3.0) * M_PI * A * B * Cc;
+        const double I[3] = {m * (B * B + Cc * Cc) / 5.0, m * (A * A + Cc * Cc) / 5.0, m * (A * A + B * B) / 5.0};
+        // angular momentum L = R I R^T omega
+        double ob[3], Lw[3];
+        for (int a = 0; a < 3; ++a)
+            ob[a] = (R[a] * b.omega[0] + R[3 + a] * b.omega[1] + R[6 + a] * b.omega[2]) * I[a];
+        for (int a = 0; a < 3; ++a) Lw[a] = R[3 * a] * ob[0] + R[3 * a + 1] * ob[1] + R[3 * a + 2] * ob[2];
+        for (int a = 0; a < 3; ++a) {
+            pos[3 * i + a] = b.pos[a];
+            vel[3 * i + a] = b.vel[a];
+            om[3 * i + a] = b.omega[a];
+            L[3 * i + a] = Lw[a];
+            semi[3 * i + a] = b.semi_axes[a];
+            inertia[3 * i + a] = I[a];
+            extF[3 * i + a] = b.ext_force[a];
+            extM[3 * i + a] = b.ext_torque[a];
+        }
+        for (int k = 0; k < 4; ++k) quat[4 * i + k] = q[k];
+        mass[i] = m;
+        cell[i] = b.cell;
+        fixed[i] = b.fixed ? 1 : 0;
+    }
+    // re-mapping launch shape: about four box cells per thread for the
+    // largest body, at most ~64 blocks per SM over all bodies
+    {
+        double amax = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int a = 0; a < 3; ++a) amax = std::fmax(amax, p[i].semi_axes[a]);
+        const double side = 2.0 * amax + 7.0;
+        const double vol = side * side * side;
+        long long bpb = (long long)std::ceil(vol / (256.0 * 4.0));
+        bpb = bpb < 1 ? 1 : (bpb > 1024 ? 1024 : bpb);
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const long long cap = (long long)(sms > 0 ? sms : 1) * 64;
+        if (n > 0 && bpb * n > cap) bpb = cap / n > 0 ? cap / n : 1;
+        ctx->remap_bpb = (int)bpb;
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    drop_graph(ctx);
+    free_particles(ctx);
+    PartDev &P = ctx->P;
+    P.np = n;
+    const size_t m = n > 0 ? n : 1;
+    P.pos = part_alloc<double>(ctx, 3 * m);
+    P.quat = part_alloc<double>(ctx, 4 * m);
+    P.vel = part_alloc<double>(ctx, 3 * m);
+    P.om = part_alloc<double>(ctx, 3 * m);
+    P.L = part_alloc<double>(ctx, 3 * m);
+    P.semi = part_alloc<double>(ctx, 3 * m);
+    P.mass = part_alloc<double>(ctx, m);
+    P.inertia = part_alloc<double>(ctx, 3 * m);
+    P.extF = part_alloc<double>(ctx, 3 * m);
+    P.extM = part_alloc<double>(ctx, 3 * m);
+    P.cell = part_alloc<int>(ctx, m);
+    P.fixed = part_alloc<int>(ctx, m);
+    P.pos_old = part_alloc<double>(ctx, 3 * m);
+    P.vel_old = part_alloc<double>(ctx, 3 * m);
+    P.om_old = part_alloc<double>(ctx, 3 * m);
+    P.quat_old = part_alloc<double>(ctx, 4 * m);
+    P.acc = part_alloc<double>(ctx, 6 * m);
+    P.last = part_alloc<double>(ctx, 6 * m);
+    P.region = part_alloc<int>(ctx, 6 * m);
+    for (void *b : ctx->part_bufs)
+        if (!b) {
+            free_particles(ctx);
+            return fail(ctx, LBM_ERR_OOM, "particle buffers");
+        }
+    ctx->np = n;
+    auto up = [&](void *dst, const void *src, size_t bytes) -> cudaError_t {
+        if (bytes == 0) return cudaSuccess;
+        return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream);
+    };
+    CK(up(P.pos, pos.data(), 8 * pos.size()));
+    CK(up(P.quat, quat.data(), 8 * quat.size()));
+    CK(up(P.vel, vel.data(), 8 * vel.size()));
+    CK(up(P.om, om.data(), 8 * om.size()));
+    CK(up(P.L, L.data(), 8 * L.size()));
+    CK(up(P.semi, semi.data(), 8 * semi.size()));
+    CK(up(P.mass, mass.data(), 8 * mass.size()));
+    CK(up(P.inertia, inertia.data(), 8 * inertia.size()));
+    CK(up(P.extF, extF.data(), 8 * extF.size()));
+    CK(up(P.extM, extM.data(), 8 * extM.size()));
+    CK(up(P.cell, cell.data(), 4 * cell.size()));
+    CK(up(P.fixed, fixed.data(), 4 * fixed.size()));
+    CK(up(P.pos_old, pos.data(), 8 * pos.size()));
+    CK(up(P.vel_old, vel.data(), 8 * vel.size()));
+    CK(up(P.om_old, om.data(), 8 * om.size()));
+    CK(up(P.quat_old, quat.data(), 8 * quat.size()));
+    CK(up(P.region, region.data(), 4 * region.size()));
+    CK(cudaMemsetAsync(P.acc, 0, sizeof(double) * 6 * m, ctx->stream));
+    CK(cudaMemsetAsync(P.last, 0, sizeof(double) * 6 * m, ctx->stream));
+    // full re-map of every lattice for the next sweep's parity
+    RemapArgs ra = remap_args(ctx);
+    const int next_odd = (int)(ctx->t & 1);
+    for (int li = 0; li < ctx->nlat; ++li) CK(launch_clear_particles(ctx->lat_h[li], ra, li, ctx->stream));
+    CK(launch_claim_all(ra, ctx->remap_bpb, ctx->stream));
+    for (int li = 0; li < ctx->nlat; ++li)
+        CK(launch_remap_full(ctx->prec, next_odd, ra, ctx->lat_h[li], li, ctx->stream));
+    ctx->launches += 3 * ctx->nlat + (n > 0 ? 1 : 0);
+    CK(cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx *ctx, int nsteps) {
+    if (!ctx) return LBM_ERR_ARG;
+    if (nsteps < 0) return fail(ctx, LBM_ERR_ARG, "nsteps < 0");
+    if (ctx->broken) return fail(ctx, LBM_ERR_STATE, "context stopped after an earlier error");
+    int left = nsteps;
+    const bool use_graph = ctx->graphs && !ctx->timing && ctx->stream != nullptr;
+    if (use_graph && left >= 2) {
+        if (ctx->t & 1) {
+            lbm_status s = enqueue_step(ctx, false);
+            if (s != LBM_OK) return s;
+            --left;
+        }
+        if (left >= 2) {
+            if (!ctx->gvalid) {
+                lbm_status s = build_graph(ctx);
+                if (s != LBM_OK) return s;
+            }
+            const int per = 2 + 2 * (ctx->np > 0 ? kernels_per_remap_step() : 0);
+            while (left >= 2) {
+                CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
+                ctx->t += 2;
+                ctx->launches += per;
+                left -= 2;
+            }
+        }
+    }
+    while (left > 0) {
+        lbm_status s = enqueue_step(ctx, ctx->timing);
+        if (s != LBM_OK) return s;
+        --left;
+    }
+    if (ctx->timing && ctx->ev_used > 4096) return harvest_timing(ctx);
+    return LBM_OK;
+}
+
+lbm_status lbm_sync(lbm_ctx *ctx) {
+    if (!ctx) return LBM_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return check_err_word(ctx);
+}
+
+lbm_status lbm_get_forces(lbm_ctx *ctx, double *force3n, double *torque3n, int n) {
+    if (!ctx) return LBM_ERR_ARG;
+    if (n < 0 || n > ctx->np) return fail(ctx, LBM_ERR_ARG, "n out of range");
+    if (n == 0) return LBM_OK;
+    std::vector<double> buf(6 * (size_t)n);
+    CK(cudaMemcpyAsync(buf.data(), ctx->P.last, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < n; ++i)
+        for (int a = 0; a < 3; ++a) {
+            if (force3n) force3n[3 * i + a] = buf[6 * i + a];
+            if (torque3n) torque3n[3 * i + a] = buf[6 * i + 3 + a];
+        }
+    return check_err_word(ctx);
+}
+
+lbm_status lbm_get_wall_forces(lbm_ctx *ctx, int cell, double *f6) {
+    if (!ctx || !f6) return LBM_ERR_ARG;
+    if (cell < 0 || cell >= ctx->nlat) return fail(ctx, LBM_ERR_ARG, "cell out of range");
+    CK(cudaMemcpyAsync(f6, ctx->wall_last + 6 * cell, sizeof(double) * 6, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_get_particles(lbm_ctx *ctx, lbm_particle *p, int n) {
+    if (!ctx || (n > 0 && !p)) return LBM_ERR_ARG;
+    if (n < 0 || n > ctx->np) return fail(ctx, LBM_ERR_ARG, "n out of range");
+    if (n == 0) return LBM_OK;
+    std::vector<double> pos(3 * n), quat(4 * n), vel(3 * n), om(3 * n), semi(3 * n), mass(n), eF(3 * n), eM(3 * n);
+    std::vector<int> cell(n), fixed(n);
+    const PartDev &P = ctx->P;
+    CK(cudaMemcpyAsync(pos.data(), P.pos, 24 * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(quat.data(), P.quat, 32 * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(vel.data(), P.vel, 24 * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(om.data(), P.om, 24 * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(semi.data(), P.semi, 24 * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(mass.data(), P.mass, 8 * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(eF.data(), P.extF, 24 * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(eM.data(), P.extM, 24 * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(cell.data(), P.cell, 4 * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(fixed.data(), P.fixed, 4 * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < n; ++i) {
+        lbm_particle &b = p[i];
+        for (int a = 0; a < 3; ++a) {
+            b.pos[a] = pos[3 * i + a];
+            b.vel[a] = vel[3 * i + a];
+            b.omega[a] = om[3 * i + a];
+            b.semi_axes[a] = semi[3 * i + a];
+            b.ext_force[a] = eF[3 * i + a];
+            b.ext_torque[a] = eM[3 * i + a];
+        }
+        for (int k = 0; k < 4; ++k) b.quat[k] = quat[4 * i + k];
+        b.density = mass[i] / ((4.0 / 3.0) * M_PI * b.semi_axes[0] * b.semi_axes[1] * b.semi_axes[2]);
+        b.cell = cell[i];
+        b.fixed = fixed[i];
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_set_external(lbm_ctx *ctx, const double *force3n, const double *torque3n, int n) {
+    if (!ctx) return LBM_ERR_ARG;
+    if (n < 0 || n > ctx->np) return fail(ctx, LBM_ERR_ARG, "n out of range");
+    if (n == 0) return LBM_OK;
+    if (force3n) CK(cudaMemcpyAsync(ctx->P.extF, force3n, 24 * n, cudaMemcpyHostToDevice, ctx->stream));
+    if (torque3n) CK(cudaMemcpyAsync(ctx->P.extM, torque3n, 24 * n, cudaMemcpyHostToDevice, ctx->stream));
+    // pageable host memory: the copy has been staged when cudaMemcpyAsync returns
+    return LBM_OK;
+}
+
+lbm_status lbm_get_fields(lbm_ctx *ctx, int cell, double *rho, double *u3, uint8_t *flags, uint32_t *pid,
+                          double *pdfs) {
+    if (!ctx) return LBM_ERR_ARG;
+    if (cell < 0 || cell >= ctx->nlat) return fail(ctx, LBM_ERR_ARG, "cell out of range");
+    const LatDev &h = ctx->lat_h[cell];
+    const size_t n = h.n;
+    const size_t bytes = (rho ? 8 * n : 0) + (u3 ? 24 * n : 0) + (pdfs ? 8 * Q * n : 0) + (flags ? n : 0) + 64;
+    char *scratch = (char *)dalloc(ctx, bytes);
+    if (!scratch) return fail(ctx, LBM_ERR_OOM, "field scratch");
+    double *d_rho = nullptr, *d_u = nullptr, *d_pdfs = nullptr;
+    uint8_t *d_fl = nullptr;
+    size_t off = 0;
+    if (rho) { d_rho = (double *)(scratch + off); off += 8 * n; }
+    if (u3) { d_u = (double *)(scratch + off); off += 24 * n; }
+    if (pdfs) { d_pdfs = (double *)(scratch + off); off += 8 * Q * n; }
+    if (flags) { d_fl = (uint8_t *)(scratch + off); off += n; }
+    lbm_status st = LBM_OK;
+    cudaError_t e = launch_canonical(ctx->prec, (int)(ctx->t & 1), h, ctx->lat_d + cell, ctx->f, ctx->flags,
+                                     ctx->pid, d_rho, d_u, d_fl, d_pdfs, ctx->stream);
+    ctx->launches += 1;
+    if (e == cudaSuccess && rho) e = cudaMemcpyAsync(rho, d_rho, 8 * n, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess && u3) e = cudaMemcpyAsync(u3, d_u, 24 * n, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess && pdfs) e = cudaMemcpyAsync(pdfs, d_pdfs, 8 * Q * n, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess && flags) e = cudaMemcpyAsync(flags, d_fl, n, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess && pid)
+        e = cudaMemcpyAsync(pid, ctx->pid + h.c_off, 4 * n, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) st = fail(ctx, LBM_ERR_CUDA, std::string("get_fields: ") + cudaGetErrorString(e));
+    dfree(ctx, scratch);
+    return st;
+}
+
+lbm_status lbm_set_pdfs(lbm_ctx *ctx, int cell, const double *pdfs) {
+    if (!ctx || !pdfs) return LBM_ERR_ARG;
+    if (cell < 0 || cell >= ctx->nlat) return fail(ctx, LBM_ERR_ARG, "cell out of range");
+    const LatDev &h = ctx->lat_h[cell];
+    const size_t bytes = 8 * Q * (size_t)h.n;
+    double *d = (double *)dalloc(ctx, bytes);
+    if (!d) return fail(ctx, LBM_ERR_OOM, "pdf scratch");
+    cudaError_t e = cudaMemcpyAsync(d, pdfs, bytes, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess)
+        e = launch_set_pdfs(ctx->prec, (int)(ctx->t & 1), h, ctx->lat_d + cell, ctx->f, ctx->flags, d, ctx->stream);
+    ctx->launches += 1;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    dfree(ctx, d);
+    if (e != cudaSuccess) return fail(ctx, LBM_ERR_CUDA, std::string("set_pdfs: ") + cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+lbm_status lbm_get_links(lbm_ctx *ctx, int cell, int32_t *idx, int8_t *q, uint32_t *pid, int cap, int *count) {
+    if (!ctx || !count || cap < 0) return LBM_ERR_ARG;
+    if (cell < 0 || cell >= ctx->nlat) return fail(ctx, LBM_ERR_ARG, "cell out of range");
+    const LatDev &h = ctx->lat_h[cell];
+    const int nblocks = (h.n + 255) / 256;
+    const size_t cap_sz = cap > 0 ? (size_t)cap : 0;
+    const size_t bytes = 4 * (size_t)nblocks + 16 + cap_sz * (4 + 4 + 1) + 64;
+    char *scratch = (char *)dalloc(ctx, bytes);
+    if (!scratch) return fail(ctx, LBM_ERR_OOM, "link scratch");
+    int *bc = (int *)scratch;
+    int *total = bc + nblocks;
+    int32_t *d_idx = (int32_t *)(scratch + 4 * (size_t)nblocks + 16);
+    uint32_t *d_pid = (uint32_t *)(d_idx + cap_sz);
+    int8_t *d_q = (int8_t *)(d_pid + cap_sz);
+    cudaError_t e = launch_links(h, ctx->lat_d + cell, ctx->flags, ctx->pid, bc, nblocks, cap ? d_idx : nullptr,
+                                 cap ? d_q : nullptr, cap ? d_pid : nullptr, cap, total, ctx->stream);
+    ctx->launches += 3;
+    int tot = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&tot, total, 4, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    const int nw = tot < cap ? tot : cap;
+    if (e == cudaSuccess && nw > 0 && idx) e = cudaMemcpyAsync(idx, d_idx, 4 * (size_t)nw, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess && nw > 0 && q) e = cudaMemcpyAsync(q, d_q, (size_t)nw, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess && nw > 0 && pid) e = cudaMemcpyAsync(pid, d_pid, 4 * (size_t)nw, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    dfree(ctx, scratch);
+    if (e != cudaSuccess) return fail(ctx, LBM_ERR_CUDA, std::string("get_links: ") + cudaGetErrorString(e));
+    *count = tot;
+    return LBM_OK;
+}
+
+lbm_status lbm_get_info(lbm_ctx *ctx, lbm_info *info) {
+    if (!ctx || !info) return LBM_ERR_ARG;
+    long long n = 0;
+    for (auto &L : ctx->lat_h) n += L.n;
+    info->ncells_total = n;
+    info->nfluid_hint = -1;
+    info->nlattices = ctx->nlat;
+    info->nparticles = ctx->np;
+    info->steps_done = ctx->t;
+    info->device_bytes = ctx->device_bytes;
+    info->sweep_grid = ctx->grid;
+    info->sweep_block = ctx->block;
+    info->bytes_per_population = ctx->esize;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_launch(lbm_ctx *ctx, int block, int grid) {
+    if (!ctx) return LBM_ERR_ARG;
+    if (block < 32 || block > 256 || block % 32) return fail(ctx, LBM_ERR_ARG, "block must be a multiple of 32 in [32, 256]");
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->block = block;
+    fill_tiles(ctx);
+    lbm_status s = upload_lattices(ctx);
+    if (s != LBM_OK) return s;
+    ctx->grid = grid > 0 ? (grid < ctx->ntiles ? grid : ctx->ntiles) : default_grid(ctx);
+    drop_graph(ctx);
+    return LBM_OK;
+}
+
+lbm_status lbm_autotune(lbm_ctx *ctx, int *block_out, int *grid_out) {
+    if (!ctx) return LBM_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->stream));
+    // back up the populations; sweeps below run on the live buffers
+    const size_t fbytes = (size_t)ctx->f_elems * ctx->esize;
+    void *backup = dalloc(ctx, fbytes);
+    if (!backup) return fail(ctx, LBM_ERR_OOM, "autotune backup");
+    CK(cudaMemcpyAsync(backup, ctx->f, fbytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int blocks[] = {128, 192, 256};
+    double best = 1e30;
+    int bb = ctx->block, bg = ctx->grid;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (int blk : blocks) {
+        lbm_status s = lbm_set_launch(ctx, blk, 0);
+        if (s != LBM_OK) break;
+        const int occ = sweep_max_active_blocks(ctx->prec, 1, blk);
+        if (occ <= 0) continue;
+        const int grids[] = {sms * occ, 2 * sms * occ, ctx->ntiles};
+        for (int gr : grids) {
+            if (gr > ctx->ntiles) gr = ctx->ntiles;
+            ctx->grid = gr;
+            SweepArgs sa = sweep_args(ctx);
+            for (int w = 0; w < 2; ++w) {
+                launch_sweep(ctx->prec, 0, sa, gr, blk, ctx->stream);
+                launch_sweep(ctx->prec, 1, sa, gr, blk, ctx->stream);
+            }
+            CK(cudaEventRecord(e0, ctx->stream));
+            const int reps = 4;
+            for (int r = 0; r < reps; ++r) {
+                launch_sweep(ctx->prec, 0, sa, gr, blk, ctx->stream);
+                launch_sweep(ctx->prec, 1, sa, gr, blk, ctx->stream);
+            }
+            CK(cudaEventRecord(e1, ctx->stream));
+            CK(cudaEventSynchronize(e1));
+            ctx->launches += 2 * (2 + reps);
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) {
+                best = ms;
+                bb = blk;
+                bg = gr;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    lbm_status s = lbm_set_launch(ctx, bb, bg);
+    CK(cudaMemcpyAsync(ctx->f, backup, fbytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (ctx->np > 0) CK(cudaMemsetAsync(ctx->P.acc, 0, sizeof(double) * 6 * ctx->np, ctx->stream));
+    CK(cudaMemsetAsync(ctx->wall_acc, 0, sizeof(double) * 6 * ctx->nlat, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    dfree(ctx, backup);
+    if (block_out) *block_out = bb;
+    if (grid_out) *grid_out = bg;
+    return s;
+}
+
+lbm_status lbm_set_graphs(lbm_ctx *ctx, int enable) {
+    if (!ctx) return LBM_ERR_ARG;
+    ctx->graphs = enable != 0 && ctx->stream != nullptr;
+    if (!ctx->graphs) drop_graph(ctx);
+    return LBM_OK;
+}
+
+lbm_status lbm_set_sweep_timing(lbm_ctx *ctx, int enable) {
+    if (!ctx) return LBM_ERR_ARG;
+    lbm_status s = harvest_timing(ctx);
+    if (s != LBM_OK) return s;
+    ctx->timing = enable != 0;
+    ctx->ms_acc = 0.0;
+    ctx->timed_launches = 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_get_sweep_timing(lbm_ctx *ctx, double *ms, long long *launches) {
+    if (!ctx) return LBM_ERR_ARG;
+    lbm_status s = harvest_timing(ctx);
+    if (s != LBM_OK) return s;
+    if (ms) *ms = ctx->ms_acc;
+    if (launches) *launches = ctx->timed_launches;
+    ctx->ms_acc = 0.0;
+    ctx->timed_launches = 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_get_launch_count(lbm_ctx *ctx, long long *launches) {
+    if (!ctx || !launches) return LBM_ERR_ARG;
+    *launches = ctx->launches;
+    return LBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,175 @@
+// lbm_internal.cuh -- device-side types of the GB300 LBM / moving-particle
+// library.  Lattice Boltzmann method with fully resolved rigid particles,
+// Sec. 4 of Bartuschat et al. ("Two computational models for simulating the
+// tumbling motion of elongated particles in fluids").
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/lbm.h"
+
+namespace lbm {
+
+constexpr int Q = 19;
+
+// D3Q19 (Sec. 4.1).  Numbering: 0 rest, 1..6 axis pairs, 7..18 diagonal pairs;
+// q and opp(q) are adjacent so opp is arithmetic.  Indexed only with
+// compile-time q (unrolled loops), so the tables fold into immediates.
+__host__ __device__ constexpr int cx(int q) {
+    constexpr int t[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+    return t[q];
+}
+__host__ __device__ constexpr int cy(int q) {
+    constexpr int t[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+    return t[q];
+}
+__host__ __device__ constexpr int cz(int q) {
+    constexpr int t[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+    return t[q];
+}
+__host__ __device__ constexpr int opp(int q) { return q == 0 ? 0 : ((q & 1) ? q + 1 : q - 1); }
+__host__ __device__ constexpr double wq(int q) {
+    return q == 0 ? 1.0 / 3.0 : (q <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+
+// Internal cell flags (one byte per cell).
+constexpr uint8_t F_NEAR = 1;     // fluid cell with at least one wall/obstacle neighbour
+constexpr uint8_t F_SOLID = 2;    // wall or obstacle cell (not collided)
+constexpr uint8_t F_CHANGED = 4;  // touched by this step's re-mapping (transient)
+constexpr uint8_t F_WALL = 8;     // static wall layer (never re-mapped)
+
+constexpr uint32_t PID_FLUID = LBM_PID_FLUID;
+constexpr uint32_t PID_WALL_YLO = LBM_PID_WALL_YLO;
+constexpr uint32_t PID_WALL_YHI = LBM_PID_WALL_YHI;
+constexpr uint32_t PID_WALL = LBM_PID_WALL;
+
+// Division by a runtime-invariant divisor with one multiply-high
+// (Granlund & Montgomery, PLDI 1994, round-up variant): exact for n < 2^31.
+struct FastDiv {
+    uint32_t d, m, s;
+    __host__ void init(uint32_t div) {
+        d = div;
+        s = 0;
+        while ((1ull << s) < div) ++s;
+        m = (uint32_t)((((1ull << 32) * ((1ull << s) - div)) / div) + 1);
+    }
+    __device__ __forceinline__ uint32_t div(uint32_t n) const {
+        return (__umulhi(n, m) + n) >> s;
+    }
+};
+
+// One lattice of a context (device-resident table, one entry per lattice).
+struct LatDev {
+    int nx, ny, nz;
+    int n;                 // nx*ny*nz
+    int npad;              // population plane stride (elements)
+    int tile0;             // first sweep tile of this lattice
+    long long f_off;       // element offset of plane 0 in the population arena
+    long long c_off;       // cell offset in the flag / id arenas
+    FastDiv divx, divxy;   // idx -> (x, y, z)
+    int px, py, pz;        // periodic flags
+    int pad0;
+    double omega, omega_odd, rho0;
+    double wlo[3], whi[3], g[3];
+};
+
+// Rigid bodies, structure of arrays, FP64 throughout.
+struct PartDev {
+    int np;
+    int pad0;
+    double *pos, *quat, *vel, *om, *L;   // current state (3/4/3/3/3 per body)
+    double *semi, *mass, *inertia;       // shape: semi-axes, mass, body inertia diag
+    double *extF, *extM;                 // external loads
+    int *cell, *fixed;
+    double *pos_old, *vel_old, *om_old, *quat_old; // state before this step's update
+    double *acc;       // 6 per body: hydrodynamic F, M summed by the sweep
+    double *last;      // 6 per body: F, M of the last completed step
+    int *region;       // 6 per body: lo[3], ext[3] of the re-mapping box
+};
+
+struct SweepArgs {
+    LatDev lat0;             // copy of lattice 0 (used when nlat == 1)
+    const LatDev *lat;
+    int nlat;
+    int ntiles;
+    void *f;                 // population arena (storage type)
+    const uint8_t *flags;
+    const uint32_t *pid;
+    PartDev P;
+    double *wall_acc;        // 6 per lattice: y-low wall F, y-high wall F
+    uint32_t *err;           // device error word
+};
+
+// Storage forms: every form holds g_q = f_q - w_q rho0 (the offset from rest).
+template <int PREC> struct Store;
+template <> struct Store<LBM_F64> {
+    using T = double;
+    using C = double;
+    static __device__ __forceinline__ C ld(const T *p) { return *p; }
+    static __device__ __forceinline__ void st(T *p, C v) { *p = v; }
+};
+template <> struct Store<LBM_F32> {
+    using T = float;
+    using C = float;
+    static __device__ __forceinline__ C ld(const T *p) { return *p; }
+    static __device__ __forceinline__ void st(T *p, C v) { *p = v; }
+};
+template <> struct Store<LBM_F16_OFFSET> {
+    using T = __half;
+    using C = float;
+    static __device__ __forceinline__ C ld(const T *p) { return __half2float(*p); }
+    static __device__ __forceinline__ void st(T *p, C v) { *p = __float2half_rn(v); }
+};
+template <> struct Store<LBM_BF16_OFFSET> {
+    using T = __nv_bfloat16;
+    using C = float;
+    static __device__ __forceinline__ C ld(const T *p) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ void st(T *p, C v) { *p = __float2bfloat16_rn(v); }
+};
+
+// Device error-word bits.
+constexpr uint32_t ERR_NONFINITE = 1u;
+constexpr uint32_t ERR_TIMEOUT = 2u;
+
+// --- launchers (defined in the .cu files) ---------------------------------
+cudaError_t launch_sweep(int prec, int parity, const SweepArgs &a, int grid, int block,
+                         cudaStream_t s);
+int sweep_max_active_blocks(int prec, int parity, int block);
+
+struct RemapArgs {
+    const LatDev *lat;
+    void *f;
+    uint8_t *flags;
+    uint32_t *pid;
+    uint32_t *pid_prev;
+    PartDev P;
+    double *wall_acc;
+    double *wall_last;
+    int nlat;
+    uint32_t *err;
+};
+cudaError_t launch_rigid_body(const RemapArgs &a, cudaStream_t s);
+cudaError_t launch_remap_step(int prec, int next_parity, const RemapArgs &a, int blocks_per_body,
+                              cudaStream_t s);
+cudaError_t launch_clear_particles(const LatDev &h, const RemapArgs &a, int lat_index,
+                                   cudaStream_t s);
+cudaError_t launch_claim_all(const RemapArgs &a, int blocks_per_body, cudaStream_t s);
+cudaError_t launch_remap_full(int prec, int next_parity, const RemapArgs &a, const LatDev &h,
+                              int lat_index, cudaStream_t s);
+cudaError_t launch_init_cells(const LatDev &h, const LatDev *d, uint8_t *flags, uint32_t *pid,
+                              uint32_t *pid_prev, cudaStream_t s);
+cudaError_t launch_canonical(int prec, int next_parity, const LatDev &h, const LatDev *d,
+                             const void *f, const uint8_t *flags, const uint32_t *pid,
+                             double *rho, double *u3, uint8_t *flags_out, double *pdfs,
+                             cudaStream_t s);
+cudaError_t launch_set_pdfs(int prec, int next_parity, const LatDev &h, const LatDev *d, void *f,
+                            const uint8_t *flags, const double *pdfs, cudaStream_t s);
+cudaError_t launch_links(const LatDev &h, const LatDev *d, const uint8_t *flags,
+                         const uint32_t *pid, int *block_counts, int nblocks, int32_t *idx,
+                         int8_t *q, uint32_t *pid_out, int cap, int *total, cudaStream_t s);
+int kernels_per_remap_step();
+
+}  // namespace lbm

@@ -1,0 +1,807 @@
+// lbm_particles.cu -- everything of a time step besides the sweep:
+//  * the rigid-body update of every particle (Sec. 4.3; the integrator is not
+//    given in the paper: semi-implicit Euler on U and on the world-frame
+//    angular momentum, quaternion exponential update, all FP64);
+//  * the re-mapping of obstacle cells from the new poses (Sec. 4.2: a cell is
+//    an obstacle cell iff its centre is inside a body), with equilibrium
+//    refill of uncovered cells at rho0 and the surface velocity of the
+//    previous time step (Sec. 4.2, last paragraph);
+//  * field export in canonical form, population import, link compaction.
+//
+// Re-mapping runs over each body's box (union of its old and new bounding
+// boxes, plus margin) in four passes separated by kernel boundaries:
+//   A uncover: cells of body p no longer inside p become fluid (pid_prev = p);
+//   B claim:   cells inside p take id min(id, p) (lowest index wins);
+//   C fix-up:  every cell whose fluid/obstacle status changed is processed once
+//              (by the body that uncovered or covered it) and its populations
+//              are rewritten in the AA layout of the next sweep;
+//   D flags:   flag bytes (obstacle / near-obstacle) are recomputed.
+//
+// AA layout between steps.  After an odd sweep the next sweep is even and
+// reads f_q(x) from slot q of x, so a refill writes all 19 slots of x.  After
+// an even sweep the next (odd) sweep reads f_p(z) from slot opp(p) of
+// z - c_p if that cell is fluid, else from slot p of z.  Each lattice link
+// {z, z' = z - c_p} therefore owns two slots A = (opp(p), z') and B = (p, z):
+// with both cells fluid A holds f_p(z) and B holds f_opp(p)(z'); with only z
+// fluid B holds f_p(z); with only z' fluid A holds f_opp(p)(z').  When a status
+// changes, pass C reads the link's logical values under the old statuses and
+// rewrites them under the new ones.
+#include "lbm_internal.cuh"
+
+namespace lbm {
+
+namespace {
+
+__device__ __forceinline__ int wrapc(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+__device__ __forceinline__ double min_image_rn(double d, int n, int periodic) {
+    if (periodic) {
+        const double h = 0.5 * (double)n;
+        if (d > h)
+            d = __dsub_rn(d, (double)n);
+        else if (d < -h)
+            d = __dadd_rn(d, (double)n);
+    }
+    return d;
+}
+
+// Rotation matrix of a unit quaternion (w,x,y,z), every operation rounded
+// separately in a fixed order so that the obstacle mapping is reproducible
+// bit for bit.
+__device__ __forceinline__ void quat_matrix_rn(const double *q, double R[9]) {
+    const double w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(__dmul_rn(y, y), __dmul_rn(z, z))));
+    R[1] = __dmul_rn(2.0, __dsub_rn(__dmul_rn(x, y), __dmul_rn(w, z)));
+    R[2] = __dmul_rn(2.0, __dadd_rn(__dmul_rn(x, z), __dmul_rn(w, y)));
+    R[3] = __dmul_rn(2.0, __dadd_rn(__dmul_rn(x, y), __dmul_rn(w, z)));
+    R[4] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(__dmul_rn(x, x), __dmul_rn(z, z))));
+    R[5] = __dmul_rn(2.0, __dsub_rn(__dmul_rn(y, z), __dmul_rn(w, x)));
+    R[6] = __dmul_rn(2.0, __dsub_rn(__dmul_rn(x, z), __dmul_rn(w, y)));
+    R[7] = __dmul_rn(2.0, __dadd_rn(__dmul_rn(y, z), __dmul_rn(w, x)));
+    R[8] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y))));
+}
+
+// Cell centre (i,j,k) inside the ellipsoid: (p0/a)^2 + (p1/b)^2 + (p2/c)^2 <= 1
+// with p = R^T d and d the nearest-image displacement from the centre.
+__device__ __forceinline__ bool inside_rn(const LatDev &L, const double *pos, const double R[9],
+                                          const double *semi, int i, int j, int k) {
+    const double d0 = min_image_rn(__dsub_rn((double)i, pos[0]), L.nx, L.px);
+    const double d1 = min_image_rn(__dsub_rn((double)j, pos[1]), L.ny, L.py);
+    const double d2 = min_image_rn(__dsub_rn((double)k, pos[2]), L.nz, L.pz);
+    const double p0 = __dadd_rn(__dadd_rn(__dmul_rn(R[0], d0), __dmul_rn(R[3], d1)), __dmul_rn(R[6], d2));
+    const double p1 = __dadd_rn(__dadd_rn(__dmul_rn(R[1], d0), __dmul_rn(R[4], d1)), __dmul_rn(R[7], d2));
+    const double p2 = __dadd_rn(__dadd_rn(__dmul_rn(R[2], d0), __dmul_rn(R[5], d1)), __dmul_rn(R[8], d2));
+    const double t0 = __ddiv_rn(p0, semi[0]), t1 = __ddiv_rn(p1, semi[1]), t2 = __ddiv_rn(p2, semi[2]);
+    const double s = __dadd_rn(__dadd_rn(__dmul_rn(t0, t0), __dmul_rn(t1, t1)), __dmul_rn(t2, t2));
+    return s <= 1.0;
+}
+
+// The same test decided in FP32 wherever that is safe: the FP32 value of s
+// differs from the FP64 one by far less than 1e-4 for cells within a body's
+// box (|d| below ~10^2, semi-axes >= ~1), so outside a band |s - 1| <= 1e-3
+// the FP32 decision equals the FP64 one, and inside the band the exact FP64
+// test decides.  The result is bit-identical to inside_rn.
+struct BodyF32 {
+    float R[9];
+    float inv[3];
+};
+
+__device__ __forceinline__ void body_f32(const double R[9], const double *semi, BodyF32 &b) {
+    for (int k = 0; k < 9; ++k) b.R[k] = (float)R[k];
+    for (int k = 0; k < 3; ++k) b.inv[k] = (float)(1.0 / semi[k]);
+}
+
+__device__ __forceinline__ bool inside_fast(const LatDev &L, const double *pos, const double R[9],
+                                            const double *semi, const BodyF32 &b, int i, int j, int k) {
+    const float d0 = (float)min_image_rn((double)i - pos[0], L.nx, L.px);
+    const float d1 = (float)min_image_rn((double)j - pos[1], L.ny, L.py);
+    const float d2 = (float)min_image_rn((double)k - pos[2], L.nz, L.pz);
+    const float t0 = (b.R[0] * d0 + b.R[3] * d1 + b.R[6] * d2) * b.inv[0];
+    const float t1 = (b.R[1] * d0 + b.R[4] * d1 + b.R[7] * d2) * b.inv[1];
+    const float t2 = (b.R[2] * d0 + b.R[5] * d1 + b.R[8] * d2) * b.inv[2];
+    const float s = t0 * t0 + t1 * t1 + t2 * t2;
+    if (s < 0.999f) return true;
+    if (s > 1.001f) return false;
+    return inside_rn(L, pos, R, semi, i, j, k);
+}
+
+// Half extents of the world-aligned bounding box of a rotated ellipsoid.
+__device__ __forceinline__ void aabb_half(const double R[9], const double *semi, double h[3]) {
+    for (int a = 0; a < 3; ++a) {
+        const double e0 = R[3 * a + 0] * semi[0], e1 = R[3 * a + 1] * semi[1], e2 = R[3 * a + 2] * semi[2];
+        h[a] = sqrt(e0 * e0 + e1 * e1 + e2 * e2);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// rigid-body update (one thread per body) and wall-force hand-over
+// ---------------------------------------------------------------------------
+
+__global__ void rigid_body_kernel(RemapArgs a) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < a.nlat) {
+        for (int k = 0; k < 6; ++k) {
+            a.wall_last[6 * t + k] = a.wall_acc[6 * t + k];
+            a.wall_acc[6 * t + k] = 0.0;
+        }
+    }
+    const PartDev &P = a.P;
+    if (t >= P.np) return;
+    double *acc = P.acc + 6 * t, *last = P.last + 6 * t;
+    double F[3], M[3];
+    bool finite = true;
+    for (int k = 0; k < 3; ++k) {
+        last[k] = acc[k];
+        last[3 + k] = acc[3 + k];
+        F[k] = acc[k] + P.extF[3 * t + k];
+        M[k] = acc[3 + k] + P.extM[3 * t + k];
+        acc[k] = 0.0;
+        acc[3 + k] = 0.0;
+        finite = finite && isfinite(F[k]) && isfinite(M[k]);
+    }
+    double *pos = P.pos + 3 * t, *vel = P.vel + 3 * t, *om = P.om + 3 * t, *L = P.L + 3 * t;
+    double *q = P.quat + 4 * t;
+    for (int k = 0; k < 3; ++k) {
+        P.pos_old[3 * t + k] = pos[k];
+        P.vel_old[3 * t + k] = vel[k];
+        P.om_old[3 * t + k] = om[k];
+    }
+    for (int k = 0; k < 4; ++k) P.quat_old[4 * t + k] = q[k];
+
+    const LatDev &Lt = a.lat[P.cell[t]];
+    double Rold[9];
+    quat_matrix_rn(q, Rold);
+    const double *semi = P.semi + 3 * t;
+    double hold[3], cold[3] = {pos[0], pos[1], pos[2]};
+    aabb_half(Rold, semi, hold);
+
+    if (!P.fixed[t]) {
+        const double m = P.mass[t];
+        const double *I = P.inertia + 3 * t;
+        for (int k = 0; k < 3; ++k) vel[k] += F[k] / m;
+        for (int k = 0; k < 3; ++k) pos[k] += vel[k];
+        for (int k = 0; k < 3; ++k) L[k] += M[k];
+        // omega = R diag(1/I) R^T L with the orientation before the update
+        double lb[3];
+        for (int k = 0; k < 3; ++k)
+            lb[k] = (Rold[k] * L[0] + Rold[3 + k] * L[1] + Rold[6 + k] * L[2]) / I[k];
+        for (int k = 0; k < 3; ++k)
+            om[k] = Rold[3 * k] * lb[0] + Rold[3 * k + 1] * lb[1] + Rold[3 * k + 2] * lb[2];
+        const double th = sqrt(om[0] * om[0] + om[1] * om[1] + om[2] * om[2]);
+        double dq[4] = {1.0, 0.0, 0.0, 0.0};
+        if (th > 0.0) {
+            double sh, ch;
+            sincos(0.5 * th, &sh, &ch);
+            sh /= th;
+            dq[0] = ch;
+            dq[1] = om[0] * sh;
+            dq[2] = om[1] * sh;
+            dq[3] = om[2] * sh;
+        }
+        double nq[4];
+        nq[0] = dq[0] * q[0] - (dq[1] * q[1] + dq[2] * q[2] + dq[3] * q[3]);
+        nq[1] = dq[0] * q[1] + q[0] * dq[1] + (dq[2] * q[3] - dq[3] * q[2]);
+        nq[2] = dq[0] * q[2] + q[0] * dq[2] + (dq[3] * q[1] - dq[1] * q[3]);
+        nq[3] = dq[0] * q[3] + q[0] * dq[3] + (dq[1] * q[2] - dq[2] * q[1]);
+        const double nrm = sqrt(nq[0] * nq[0] + nq[1] * nq[1] + nq[2] * nq[2] + nq[3] * nq[3]);
+        for (int k = 0; k < 4; ++k) q[k] = nq[k] / nrm;
+        const int dims[3] = {Lt.nx, Lt.ny, Lt.nz}, per[3] = {Lt.px, Lt.py, Lt.pz};
+        for (int k = 0; k < 3; ++k)
+            if (per[k]) {
+                if (pos[k] >= dims[k])
+                    pos[k] -= dims[k];
+                else if (pos[k] < 0.0)
+                    pos[k] += dims[k];
+            }
+        for (int k = 0; k < 3; ++k) finite = finite && isfinite(pos[k]) && isfinite(om[k]);
+    }
+    if (!finite) atomicOr(a.err, ERR_NONFINITE);
+
+    // re-mapping box: union of old and new bounding boxes, margin 2 cells
+    double Rnew[9], hnew[3];
+    quat_matrix_rn(q, Rnew);
+    aabb_half(Rnew, semi, hnew);
+    const int dims[3] = {Lt.nx, Lt.ny, Lt.nz}, per[3] = {Lt.px, Lt.py, Lt.pz};
+    for (int k = 0; k < 3; ++k) {
+        double lo = fmin(cold[k] - hold[k], pos[k] - hnew[k]);
+        double hi = fmax(cold[k] + hold[k], pos[k] + hnew[k]);
+        // a wrapped centre makes the two boxes an image apart: use the new one
+        if (per[k] && fabs(cold[k] - pos[k]) > 0.5 * dims[k]) {
+            lo = fmin(pos[k] - hnew[k], pos[k] - hold[k]);
+            hi = fmax(pos[k] + hnew[k], pos[k] + hold[k]);
+        }
+        int ilo = (int)floor(lo) - 2, ihi = (int)ceil(hi) + 2;
+        if (!isfinite(lo) || !isfinite(hi)) { ilo = 0; ihi = -1; }
+        if (per[k]) {
+            if (ihi - ilo + 1 > dims[k]) { ilo = 0; ihi = dims[k] - 1; }
+        } else {
+            ilo = max(ilo, 0);
+            ihi = min(ihi, dims[k] - 1);
+        }
+        P.region[6 * t + k] = ilo;
+        P.region[6 * t + 3 + k] = max(ihi - ilo + 1, 0);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// re-mapping passes
+// ---------------------------------------------------------------------------
+
+struct RegionCell {
+    int i, j, k;
+    int idx;  // index within the lattice
+};
+
+__device__ __forceinline__ int modc(int v, int n) {
+    const int m = v % n;
+    return m < 0 ? m + n : m;
+}
+
+__device__ __forceinline__ bool region_cell(const int *reg, const LatDev &L, int r, RegionCell &c) {
+    const int e0 = reg[3], e1 = reg[4];
+    const int r0 = r % e0, r12 = r / e0;
+    const int r1 = r12 % e1, r2 = r12 / e1;
+    c.i = modc(reg[0] + r0, L.nx);
+    c.j = modc(reg[1] + r1, L.ny);
+    c.k = modc(reg[2] + r2, L.nz);
+    c.idx = c.i + L.nx * (c.j + L.ny * c.k);
+    return true;
+}
+
+// Region kernels run a 1-D grid of np * bpb blocks: body p = blockIdx.x / bpb.
+struct RegionLoop {
+    int p, first, stride;
+};
+
+__device__ __forceinline__ RegionLoop region_loop(int bpb) {
+    RegionLoop l;
+    l.p = blockIdx.x / bpb;
+    l.first = (blockIdx.x % bpb) * blockDim.x + threadIdx.x;
+    l.stride = bpb * blockDim.x;
+    return l;
+}
+
+template <int PASS>
+__global__ void remap_region_kernel(RemapArgs a, int bpb) {
+    const RegionLoop rl = region_loop(bpb);
+    const int p = rl.p;
+    const PartDev &P = a.P;
+    if (p >= P.np) return;
+    const int *reg = P.region + 6 * p;
+    const int vol = reg[3] * reg[4] * reg[5];
+    if (vol <= 0) return;
+    const LatDev &L = a.lat[P.cell[p]];
+    double R[9];
+    quat_matrix_rn(P.quat + 4 * p, R);
+    const double *pos = P.pos + 3 * p, *semi = P.semi + 3 * p;
+    BodyF32 bf;
+    body_f32(R, semi, bf);
+    for (int r = rl.first; r < vol; r += rl.stride) {
+        RegionCell c;
+        region_cell(reg, L, r, c);
+        const long long cg = L.c_off + c.idx;
+        if (PASS == 0) {  // uncover
+            if (a.pid[cg] == (uint32_t)p && !inside_fast(L, pos, R, semi, bf, c.i, c.j, c.k)) {
+                a.pid[cg] = PID_FLUID;
+                a.pid_prev[cg] = (uint32_t)p;
+                a.flags[cg] |= F_CHANGED;
+            }
+        } else {  // claim
+            if (!(a.flags[cg] & F_WALL) && inside_fast(L, pos, R, semi, bf, c.i, c.j, c.k)) {
+                const uint32_t old = atomicMin(&a.pid[cg], (uint32_t)p);
+                if (old == PID_FLUID) a.flags[cg] |= F_CHANGED;
+            }
+        }
+    }
+}
+
+// Equilibrium offset f^eq_q(rho0, u) - w_q rho0 (Eq. fequ_Incompr).
+__device__ __forceinline__ double geq(int q, double rho0, const double u[3]) {
+    const double cu = cx(q) * u[0] + cy(q) * u[1] + cz(q) * u[2];
+    const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    return wq(q) * rho0 * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+}
+
+// Refill velocity of an uncovered cell: surface velocity of its previous
+// owner, from that body's state before this step's update (zero at rest).
+__device__ __forceinline__ void refill_velocity(const RemapArgs &a, const LatDev &L, uint32_t owner,
+                                                bool at_rest, int i, int j, int k, double u[3]) {
+    u[0] = u[1] = u[2] = 0.0;
+    if (at_rest || owner >= (uint32_t)a.P.np) return;
+    const double *pos = a.P.pos_old + 3 * owner, *U = a.P.vel_old + 3 * owner,
+                 *W = a.P.om_old + 3 * owner;
+    double r[3];
+    r[0] = (double)i - pos[0];
+    r[1] = (double)j - pos[1];
+    r[2] = (double)k - pos[2];
+    const int dims[3] = {L.nx, L.ny, L.nz}, per[3] = {L.px, L.py, L.pz};
+    for (int m = 0; m < 3; ++m)
+        if (per[m]) {
+            if (r[m] > 0.5 * dims[m]) r[m] -= dims[m];
+            else if (r[m] < -0.5 * dims[m]) r[m] += dims[m];
+        }
+    u[0] = U[0] + (W[1] * r[2] - W[2] * r[1]);
+    u[1] = U[1] + (W[2] * r[0] - W[0] * r[2]);
+    u[2] = U[2] + (W[0] * r[1] - W[1] * r[0]);
+}
+
+struct Coord {
+    int i, j, k;
+};
+
+__device__ __forceinline__ int lin(const LatDev &L, int i, int j, int k) {
+    return wrapc(i, L.nx) + L.nx * (wrapc(j, L.ny) + L.ny * wrapc(k, L.nz));
+}
+
+// Pass C for one status-changed cell x (see the file comment).
+template <int PREC, int NEXT_ODD>
+__device__ void fixup_cell(const RemapArgs &a, const LatDev &L, int i, int j, int k, bool at_rest) {
+    using S = Store<PREC>;
+    using T = typename S::T;
+    T *base = reinterpret_cast<T *>(a.f) + L.f_off;
+    const long long np = L.npad;
+    const int x = i + L.nx * (j + L.ny * k);
+    const long long cx0 = L.c_off;
+    const bool old_f = !(a.flags[cx0 + x] & F_SOLID);
+    const bool new_f = a.pid[cx0 + x] == PID_FLUID;
+    if (old_f == new_f) return;
+    double ux[3];
+    if (new_f) refill_velocity(a, L, a.pid_prev[cx0 + x], at_rest, i, j, k, ux);
+
+    if (!NEXT_ODD) {
+        if (new_f)
+#pragma unroll
+            for (int q = 0; q < Q; ++q) S::st(base + q * np + x, (typename S::C)geq(q, L.rho0, ux));
+        return;
+    }
+    if (new_f) S::st(base + x, (typename S::C)geq(0, L.rho0, ux));
+#pragma unroll
+    for (int q = 1; q < Q; ++q) {
+        const int zi = i - cx(q), zj = j - cy(q), zk = k - cz(q);
+        const int z = lin(L, zi, zj, zk);
+        const bool old_z = !(a.flags[cx0 + z] & F_SOLID);
+        const bool new_z = a.pid[cx0 + z] == PID_FLUID;
+        if (old_z != new_z && z < x) continue;  // the lower index handles a doubly changed link
+        T *A = base + opp(q) * np + z;
+        T *B = base + q * np + x;
+        const double va = (double)S::ld(A), vb = (double)S::ld(B);
+        double v1 = 0.0, v2 = 0.0;
+        if (new_f) v1 = old_f ? (old_z ? va : vb) : geq(q, L.rho0, ux);
+        if (new_z) {
+            if (old_z) {
+                v2 = old_f ? vb : va;
+            } else {
+                double uz[3];
+                refill_velocity(a, L, a.pid_prev[cx0 + z], at_rest, wrapc(zi, L.nx), wrapc(zj, L.ny),
+                                wrapc(zk, L.nz), uz);
+                v2 = geq(opp(q), L.rho0, uz);
+            }
+        }
+        if (new_f && new_z) {
+            S::st(A, (typename S::C)v1);
+            S::st(B, (typename S::C)v2);
+        } else if (new_f) {
+            S::st(B, (typename S::C)v1);
+        } else if (new_z) {
+            S::st(A, (typename S::C)v2);
+        }
+    }
+}
+
+template <int PREC, int NEXT_ODD>
+__global__ void fixup_region_kernel(RemapArgs a, int bpb) {
+    const RegionLoop rl = region_loop(bpb);
+    const int p = rl.p;
+    const PartDev &P = a.P;
+    if (p >= P.np) return;
+    const int *reg = P.region + 6 * p;
+    const int vol = reg[3] * reg[4] * reg[5];
+    const LatDev &L = a.lat[P.cell[p]];
+    for (int r = rl.first; r < vol; r += rl.stride) {
+        RegionCell c;
+        region_cell(reg, L, r, c);
+        const long long cg = L.c_off + c.idx;
+        if (!(a.flags[cg] & F_CHANGED)) continue;
+        const bool old_f = !(a.flags[cg] & F_SOLID);
+        const uint32_t id = a.pid[cg];
+        const bool new_f = id == PID_FLUID;
+        if (old_f == new_f) continue;
+        // exactly one body handles each changed cell: its uncoverer or its new owner
+        const uint32_t owner = new_f ? a.pid_prev[cg] : id;
+        if (owner != (uint32_t)p) continue;
+        fixup_cell<PREC, NEXT_ODD>(a, L, c.i, c.j, c.k, false);
+    }
+}
+
+__device__ __forceinline__ uint8_t flag_of(const LatDev &L, const uint32_t *pid, long long coff, int i,
+                                           int j, int k) {
+    const uint32_t id = pid[coff + i + L.nx * (j + L.ny * k)];
+    if (id != PID_FLUID) return id >= PID_WALL ? (F_SOLID | F_WALL) : F_SOLID;
+    uint8_t f = 0;
+#pragma unroll
+    for (int q = 1; q < Q; ++q) {
+        const int n = lin(L, i + cx(q), j + cy(q), k + cz(q));
+        if (pid[coff + n] != PID_FLUID) f = F_NEAR;
+    }
+    return f;
+}
+
+__global__ void flags_region_kernel(RemapArgs a, int bpb) {
+    const RegionLoop rl = region_loop(bpb);
+    const int p = rl.p;
+    const PartDev &P = a.P;
+    if (p >= P.np) return;
+    const int *reg = P.region + 6 * p;
+    const int vol = reg[3] * reg[4] * reg[5];
+    const LatDev &L = a.lat[P.cell[p]];
+    for (int r = rl.first; r < vol; r += rl.stride) {
+        RegionCell c;
+        region_cell(reg, L, r, c);
+        const long long cg = L.c_off + c.idx;
+        if (a.flags[cg] & F_WALL) continue;
+        a.flags[cg] = flag_of(L, a.pid, L.c_off, c.i, c.j, c.k);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// whole-lattice kernels (creation, particle replacement, export)
+// ---------------------------------------------------------------------------
+
+__global__ void init_pid_kernel(const LatDev *lat, uint32_t *pid, uint32_t *pid_prev) {
+    const LatDev &L = *lat;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= L.n) return;
+    const int i = x % L.nx, j = (x / L.nx) % L.ny, k = x / (L.nx * L.ny);
+    uint32_t id = PID_FLUID;
+    if (!L.py && j == 0)
+        id = PID_WALL_YLO;
+    else if (!L.py && j == L.ny - 1)
+        id = PID_WALL_YHI;
+    else if ((!L.px && (i == 0 || i == L.nx - 1)) || (!L.pz && (k == 0 || k == L.nz - 1)))
+        id = PID_WALL;
+    pid[L.c_off + x] = id;
+    pid_prev[L.c_off + x] = PID_FLUID;
+}
+
+__global__ void flags_full_kernel(const LatDev *lat, uint8_t *flags, const uint32_t *pid) {
+    const LatDev &L = *lat;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= L.n) return;
+    const int i = x % L.nx, j = (x / L.nx) % L.ny, k = x / (L.nx * L.ny);
+    flags[L.c_off + x] = flag_of(L, pid, L.c_off, i, j, k);
+}
+
+__global__ void clear_particles_kernel(const LatDev *lat, uint8_t *flags, uint32_t *pid, uint32_t *pid_prev) {
+    const LatDev &L = *lat;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= L.n) return;
+    const long long cg = L.c_off + x;
+    const uint32_t id = pid[cg];
+    if (id < PID_WALL) {
+        pid_prev[cg] = id;
+        pid[cg] = PID_FLUID;
+        flags[cg] |= F_CHANGED;
+    }
+}
+
+template <int PREC, int NEXT_ODD>
+__global__ void fixup_full_kernel(RemapArgs a, const LatDev *lat) {
+    const LatDev &L = *lat;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= L.n) return;
+    if (!(a.flags[L.c_off + x] & F_CHANGED)) return;
+    const int i = x % L.nx, j = (x / L.nx) % L.ny, k = x / (L.nx * L.ny);
+    fixup_cell<PREC, NEXT_ODD>(a, L, i, j, k, true);
+}
+
+template <int PREC, int NEXT_ODD>
+__global__ void canonical_kernel(const LatDev *lat, const void *fv, const uint8_t *flags,
+                                 const uint32_t *pid, double *rho, double *u3, uint8_t *fl_out,
+                                 double *pdfs) {
+    using S = Store<PREC>;
+    using T = typename S::T;
+    const LatDev &L = *lat;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= L.n) return;
+    const T *base = reinterpret_cast<const T *>(fv) + L.f_off;
+    const long long np = L.npad, co = L.c_off;
+    const uint8_t fl = flags[co + x];
+    if (fl_out) fl_out[x] = (fl & F_WALL) ? LBM_FLAG_WALL : ((fl & F_SOLID) ? LBM_FLAG_PARTICLE : LBM_FLAG_FLUID);
+    const int n = L.n;
+    if (fl & F_SOLID) {
+        if (rho) rho[x] = 0.0;
+        if (u3) { u3[x] = 0.0; u3[n + x] = 0.0; u3[2 * n + x] = 0.0; }
+        if (pdfs)
+            for (int q = 0; q < Q; ++q) pdfs[(long long)q * n + x] = 0.0;
+        return;
+    }
+    const int i = x % L.nx, j = (x / L.nx) % L.ny, k = x / (L.nx * L.ny);
+    double dr = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        double g;
+        if (!NEXT_ODD) {
+            g = (double)S::ld(base + q * np + x);
+        } else {
+            const int z = lin(L, i - cx(q), j - cy(q), k - cz(q));
+            if (flags[co + z] & F_SOLID)
+                g = (double)S::ld(base + q * np + x);
+            else
+                g = (double)S::ld(base + opp(q) * np + z);
+        }
+        dr += g;
+        jx += cx(q) * g;
+        jy += cy(q) * g;
+        jz += cz(q) * g;
+        if (pdfs) pdfs[(long long)q * n + x] = g + wq(q) * L.rho0;
+    }
+    if (rho) rho[x] = L.rho0 + dr;
+    if (u3) {
+        u3[x] = jx / L.rho0 + 0.5 * L.g[0];
+        u3[n + x] = jy / L.rho0 + 0.5 * L.g[1];
+        u3[2 * n + x] = jz / L.rho0 + 0.5 * L.g[2];
+    }
+    (void)pid;
+}
+
+template <int PREC, int NEXT_ODD>
+__global__ void set_pdfs_kernel(const LatDev *lat, void *fv, const uint8_t *flags, const double *pdfs) {
+    using S = Store<PREC>;
+    using T = typename S::T;
+    const LatDev &L = *lat;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= L.n) return;
+    T *base = reinterpret_cast<T *>(fv) + L.f_off;
+    const long long np = L.npad, co = L.c_off;
+    if (flags[co + x] & F_SOLID) return;
+    const int i = x % L.nx, j = (x / L.nx) % L.ny, k = x / (L.nx * L.ny);
+    const int n = L.n;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const double g = pdfs[(long long)q * n + x] - wq(q) * L.rho0;
+        if (!NEXT_ODD) {
+            S::st(base + q * np + x, (typename S::C)g);
+        } else {
+            const int z = lin(L, i - cx(q), j - cy(q), k - cz(q));
+            if (flags[co + z] & F_SOLID)
+                S::st(base + q * np + x, (typename S::C)g);
+            else
+                S::st(base + opp(q) * np + z, (typename S::C)g);
+        }
+    }
+}
+
+// links: per-block counts, a single-block exclusive scan, then ordered writes
+__device__ __forceinline__ uint32_t link_mask(const LatDev &L, const uint8_t *flags, int x) {
+    const long long co = L.c_off;
+    if (flags[co + x] & F_SOLID) return 0;
+    const int i = x % L.nx, j = (x / L.nx) % L.ny, k = x / (L.nx * L.ny);
+    uint32_t m = 0;
+#pragma unroll
+    for (int q = 1; q < Q; ++q)
+        if (flags[co + lin(L, i + cx(q), j + cy(q), k + cz(q))] & F_SOLID) m |= 1u << q;
+    return m;
+}
+
+__global__ void link_count_kernel(const LatDev *lat, const uint8_t *flags, int *block_counts) {
+    const LatDev &L = *lat;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int c = x < L.n ? __popc(link_mask(L, flags, x)) : 0;
+    __shared__ int red[32];
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) block_counts[blockIdx.x] = v;
+    }
+}
+
+__global__ void scan_kernel(int *counts, int nblocks, int *total) {
+    // single block of 1024 threads: chunked exclusive scan
+    __shared__ int buf[1024];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nblocks; base += 1024) {
+        const int i = base + threadIdx.x;
+        const int v = i < nblocks ? counts[i] : 0;
+        buf[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = 1; o < 1024; o <<= 1) {
+            const int t = threadIdx.x >= o ? buf[threadIdx.x - o] : 0;
+            __syncthreads();
+            buf[threadIdx.x] += t;
+            __syncthreads();
+        }
+        if (i < nblocks) counts[i] = carry + buf[threadIdx.x] - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += buf[1023];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void link_write_kernel(const LatDev *lat, const uint8_t *flags, const uint32_t *pid,
+                                  const int *block_offsets, int32_t *idx_out, int8_t *q_out,
+                                  uint32_t *pid_out, int cap) {
+    const LatDev &L = *lat;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t m = x < L.n ? link_mask(L, flags, x) : 0u;
+    const int c = __popc(m);
+    __shared__ int buf[1024];
+    buf[threadIdx.x] = c;
+    __syncthreads();
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+        const int t = (int)threadIdx.x >= o ? buf[threadIdx.x - o] : 0;
+        __syncthreads();
+        buf[threadIdx.x] += t;
+        __syncthreads();
+    }
+    int pos = block_offsets[blockIdx.x] + buf[threadIdx.x] - c;
+    if (!m) return;
+    const int i = x % L.nx, j = (x / L.nx) % L.ny, k = x / (L.nx * L.ny);
+#pragma unroll
+    for (int q = 1; q < Q; ++q) {
+        if (!((m >> q) & 1u)) continue;
+        if (pos < cap) {
+            if (idx_out) idx_out[pos] = x;
+            if (q_out) q_out[pos] = (int8_t)q;
+            if (pid_out) pid_out[pos] = pid[L.c_off + lin(L, i + cx(q), j + cy(q), k + cz(q))];
+        }
+        ++pos;
+    }
+}
+
+constexpr int REMAP_BLOCK = 256;
+
+template <int PREC>
+cudaError_t remap_step_prec(int next_parity, const RemapArgs &a, int bpb, cudaStream_t s) {
+    const unsigned grid = (unsigned)bpb * (unsigned)a.P.np;
+    remap_region_kernel<0><<<grid, REMAP_BLOCK, 0, s>>>(a, bpb);
+    remap_region_kernel<1><<<grid, REMAP_BLOCK, 0, s>>>(a, bpb);
+    if (next_parity)
+        fixup_region_kernel<PREC, 1><<<grid, REMAP_BLOCK, 0, s>>>(a, bpb);
+    else
+        fixup_region_kernel<PREC, 0><<<grid, REMAP_BLOCK, 0, s>>>(a, bpb);
+    flags_region_kernel<<<grid, REMAP_BLOCK, 0, s>>>(a, bpb);
+    return cudaGetLastError();
+}
+
+template <int PREC>
+cudaError_t remap_full_prec(int next_parity, const RemapArgs &a, const LatDev &h, int li, cudaStream_t s) {
+    const LatDev *d = a.lat + li;
+    const int nb = (h.n + REMAP_BLOCK - 1) / REMAP_BLOCK;
+    if (next_parity)
+        fixup_full_kernel<PREC, 1><<<nb, REMAP_BLOCK, 0, s>>>(a, d);
+    else
+        fixup_full_kernel<PREC, 0><<<nb, REMAP_BLOCK, 0, s>>>(a, d);
+    flags_full_kernel<<<nb, REMAP_BLOCK, 0, s>>>(d, a.flags, a.pid);
+    return cudaGetLastError();
+}
+
+template <int PREC>
+cudaError_t canonical_prec(int next_parity, const LatDev &h, const LatDev *d, const void *f,
+                           const uint8_t *flags, const uint32_t *pid, double *rho, double *u3,
+                           uint8_t *fl, double *pdfs, cudaStream_t s) {
+    const int nb = (h.n + 255) / 256;
+    if (next_parity)
+        canonical_kernel<PREC, 1><<<nb, 256, 0, s>>>(d, f, flags, pid, rho, u3, fl, pdfs);
+    else
+        canonical_kernel<PREC, 0><<<nb, 256, 0, s>>>(d, f, flags, pid, rho, u3, fl, pdfs);
+    return cudaGetLastError();
+}
+
+template <int PREC>
+cudaError_t set_pdfs_prec(int next_parity, const LatDev &h, const LatDev *d, void *f,
+                          const uint8_t *flags, const double *pdfs, cudaStream_t s) {
+    const int nb = (h.n + 255) / 256;
+    if (next_parity)
+        set_pdfs_kernel<PREC, 1><<<nb, 256, 0, s>>>(d, f, flags, pdfs);
+    else
+        set_pdfs_kernel<PREC, 0><<<nb, 256, 0, s>>>(d, f, flags, pdfs);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int kernels_per_remap_step() { return 4; }
+
+cudaError_t launch_rigid_body(const RemapArgs &a, cudaStream_t s) {
+    const int n = a.P.np > a.nlat ? a.P.np : a.nlat;
+    if (n <= 0) return cudaSuccess;
+    rigid_body_kernel<<<(n + 127) / 128, 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+#define LBM_DISPATCH(prec, call)                                        \
+    switch (prec) {                                                     \
+    case LBM_F64: return call<LBM_F64>;                                 \
+    case LBM_F32: return call<LBM_F32>;                                 \
+    case LBM_F16_OFFSET: return call<LBM_F16_OFFSET>;                   \
+    case LBM_BF16_OFFSET: return call<LBM_BF16_OFFSET>;                 \
+    }                                                                   \
+    return cudaErrorInvalidValue;
+
+cudaError_t launch_remap_step(int prec, int next_parity, const RemapArgs &a, int bpb, cudaStream_t s) {
+    if (a.P.np <= 0) return cudaSuccess;
+    switch (prec) {
+    case LBM_F64: return remap_step_prec<LBM_F64>(next_parity, a, bpb, s);
+    case LBM_F32: return remap_step_prec<LBM_F32>(next_parity, a, bpb, s);
+    case LBM_F16_OFFSET: return remap_step_prec<LBM_F16_OFFSET>(next_parity, a, bpb, s);
+    case LBM_BF16_OFFSET: return remap_step_prec<LBM_BF16_OFFSET>(next_parity, a, bpb, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// Full re-map for a new particle set, in three launches: clear the particle
+// cells of each lattice, claim from the new poses (regions computed on the
+// host), then fix up populations and flags of each lattice.
+cudaError_t launch_clear_particles(const LatDev &h, const RemapArgs &a, int li, cudaStream_t s) {
+    const int nb = (h.n + REMAP_BLOCK - 1) / REMAP_BLOCK;
+    clear_particles_kernel<<<nb, REMAP_BLOCK, 0, s>>>(a.lat + li, a.flags, a.pid, a.pid_prev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_claim_all(const RemapArgs &a, int blocks_per_body, cudaStream_t s) {
+    if (a.P.np <= 0) return cudaSuccess;
+    const unsigned grid = (unsigned)blocks_per_body * (unsigned)a.P.np;
+    remap_region_kernel<1><<<grid, REMAP_BLOCK, 0, s>>>(a, blocks_per_body);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_remap_full(int prec, int next_parity, const RemapArgs &a, const LatDev &h, int li,
+                              cudaStream_t s) {
+    switch (prec) {
+    case LBM_F64: return remap_full_prec<LBM_F64>(next_parity, a, h, li, s);
+    case LBM_F32: return remap_full_prec<LBM_F32>(next_parity, a, h, li, s);
+    case LBM_F16_OFFSET: return remap_full_prec<LBM_F16_OFFSET>(next_parity, a, h, li, s);
+    case LBM_BF16_OFFSET: return remap_full_prec<LBM_BF16_OFFSET>(next_parity, a, h, li, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_init_cells(const LatDev &h, const LatDev *d, uint8_t *flags, uint32_t *pid,
+                              uint32_t *pid_prev, cudaStream_t s) {
+    const int nb = (h.n + 255) / 256;
+    init_pid_kernel<<<nb, 256, 0, s>>>(d, pid, pid_prev);
+    flags_full_kernel<<<nb, 256, 0, s>>>(d, flags, pid);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_canonical(int prec, int next_parity, const LatDev &h, const LatDev *d, const void *f,
+                             const uint8_t *flags, const uint32_t *pid, double *rho, double *u3,
+                             uint8_t *fl, double *pdfs, cudaStream_t s) {
+    switch (prec) {
+    case LBM_F64: return canonical_prec<LBM_F64>(next_parity, h, d, f, flags, pid, rho, u3, fl, pdfs, s);
+    case LBM_F32: return canonical_prec<LBM_F32>(next_parity, h, d, f, flags, pid, rho, u3, fl, pdfs, s);
+    case LBM_F16_OFFSET:
+        return canonical_prec<LBM_F16_OFFSET>(next_parity, h, d, f, flags, pid, rho, u3, fl, pdfs, s);
+    case LBM_BF16_OFFSET:
+        return canonical_prec<LBM_BF16_OFFSET>(next_parity, h, d, f, flags, pid, rho, u3, fl, pdfs, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_set_pdfs(int prec, int next_parity, const LatDev &h, const LatDev *d, void *f,
+                            const uint8_t *flags, const double *pdfs, cudaStream_t s) {
+    switch (prec) {
+    case LBM_F64: return set_pdfs_prec<LBM_F64>(next_parity, h, d, f, flags, pdfs, s);
+    case LBM_F32: return set_pdfs_prec<LBM_F32>(next_parity, h, d, f, flags, pdfs, s);
+    case LBM_F16_OFFSET: return set_pdfs_prec<LBM_F16_OFFSET>(next_parity, h, d, f, flags, pdfs, s);
+    case LBM_BF16_OFFSET: return set_pdfs_prec<LBM_BF16_OFFSET>(next_parity, h, d, f, flags, pdfs, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_links(const LatDev &h, const LatDev *d, const uint8_t *flags, const uint32_t *pid,
+                         int *block_counts, int nblocks, int32_t *idx, int8_t *q, uint32_t *pid_out,
+                         int cap, int *total, cudaStream_t s) {
+    link_count_kernel<<<nblocks, 256, 0, s>>>(d, flags, block_counts);
+    scan_kernel<<<1, 1024, 0, s>>>(block_counts, nblocks, total);
+    link_write_kernel<<<nblocks, 256, 0, s>>>(d, flags, pid, block_counts, idx, q, pid_out, cap);
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

@@ -1,0 +1,85 @@
+"""CPU checks of the C interface: the library loads, exports every function
+that include/lbm.h declares, and the binding's struct layouts match the C
+compiler's.  No compute call is made (there may be no GPU)."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lbm.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:lbm_status|const char \*)\s*(lbm_\w+)\s*\(", src, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1503_06869_gb300 import _build, lbm
+    _build.build()
+    return lbm.load()
+
+
+def test_header_declares_the_interface():
+    names = _declared()
+    for n in ("lbm_create", "lbm_create_batch", "lbm_set_particles", "lbm_step", "lbm_get_forces",
+              "lbm_get_fields", "lbm_get_links", "lbm_destroy", "lbm_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_1503_06869_gb300 import lbm
+    out = subprocess.run(["nm", "-D", "--defined-only", lbm.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\sT\s(lbm_\w+)", out))
+    for n in _declared():
+        assert n in exported, n
+        assert hasattr(lib, n)
+    assert set(_declared()) <= set(lbm.SIGNATURES)
+
+
+def test_struct_layouts_match_c(tmp_path):
+    from paper_1503_06869_gb300 import lbm
+    prog = tmp_path / "sz.c"
+    prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "lbm.h"\n'
+                    'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(lbm_grid_desc),'
+                    ' sizeof(lbm_particle), sizeof(lbm_info), offsetof(lbm_grid_desc, prec),'
+                    ' offsetof(lbm_particle, cell), offsetof(lbm_info, device_bytes));return 0;}\n')
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    got = list(map(int, subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()))
+    assert got == [C.sizeof(lbm.lbm_grid_desc), C.sizeof(lbm.lbm_particle), C.sizeof(lbm.lbm_info),
+                   lbm.lbm_grid_desc.prec.offset, lbm.lbm_particle.cell.offset,
+                   lbm.lbm_info.device_bytes.offset]
+
+
+def test_status_strings_without_gpu(lib):
+    assert lib.lbm_status_string(0) == b"ok"
+    assert lib.lbm_status_string(1) == b"invalid argument"
+
+
+def test_create_rejects_bad_arguments_before_touching_the_gpu(lib):
+    """Descriptor validation happens on the host, before any CUDA call."""
+    from paper_1503_06869_gb300 import lbm
+    from lbm_inputs import shear_lattice
+    h = C.c_void_p()
+    assert lib.lbm_create(None, C.byref(h)) == lbm.LBM_ERR_ARG
+    for mutate in (lambda d: setattr(d, "nx", 2), lambda d: setattr(d, "tau", 0.5),
+                   lambda d: setattr(d, "magic", 0.0), lambda d: setattr(d, "rho0", -1.0),
+                   lambda d: d.wall_u_hi.__setitem__(0, 0.2), lambda d: setattr(d, "prec", 9)):
+        d = lbm.grid_desc(shear_lattice(8, 8, 8, 0.8, 0.01))
+        mutate(d)
+        assert lib.lbm_create(C.byref(d), C.byref(h)) == lbm.LBM_ERR_ARG
+        assert not h.value
+    assert lib.lbm_create_batch(None, 0, C.byref(h)) == lbm.LBM_ERR_ARG
+
+
+def test_null_context_is_rejected(lib):
+    from paper_1503_06869_gb300 import lbm
+    assert lib.lbm_step(None, 1) == lbm.LBM_ERR_ARG
+    assert lib.lbm_destroy(None) == lbm.LBM_ERR_ARG
+    assert lib.lbm_last_error(None) == b"null context"
