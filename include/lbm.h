@@ -207,9 +207,12 @@ typedef struct lbm_info {
 
 lbm_status lbm_get_info(lbm_ctx *ctx, lbm_info *info);
 
-/* Sweep launch shape: block threads (multiple of 32, <= 1024) and grid blocks
- * (<= 0 selects the default: enough resident blocks for every SM).  Used by
- * the autotuner; takes effect at the next lbm_step. */
+/* Sweep launch shape.  block = 0 selects the staged sweep (tiles of 256 cells
+ * brought into shared memory by asynchronous bulk copies, several tiles in
+ * flight per block); block = 32..256 (multiple of 32) selects the direct sweep
+ * with that many threads, one cell each.  grid = number of blocks (<= 0: one
+ * resident wave on every SM).  Used by the autotuner; takes effect at the next
+ * lbm_step.  The default is the staged sweep. */
 lbm_status lbm_set_launch(lbm_ctx *ctx, int block, int grid);
 
 /* Choose the sweep launch shape by timing candidates on this context (runs

@@ -12,6 +12,12 @@
 
 using namespace lbm;
 
+// Extra elements per population plane (a multiple of 64 keeps every plane
+// start on a 256-byte boundary in all storage forms).
+#ifndef LBM_PLANE_PAD
+#define LBM_PLANE_PAD 0
+#endif
+
 struct lbm_ctx {
     lbm_precision prec = LBM_F32;
     int esize = 4;
@@ -36,7 +42,11 @@ struct lbm_ctx {
     PartDev P{};
     std::vector<void *> part_bufs;
 
+    void *f_arena = nullptr;        // population allocation: guard | planes | guard
+    long long guard = 0;            // guard band in elements on each side
+
     long long t = 0;
+    int variant = SWEEP_RING;       // sweep kernel variant
     int block = 256, grid = 0, ntiles = 0;
     int remap_bpb = 8;
 
@@ -125,11 +135,14 @@ lbm_status check_desc(const lbm_grid_desc *d, std::string &m) {
     return LBM_OK;
 }
 
+int tile_cells(const lbm_ctx *ctx) { return ctx->variant == SWEEP_DIRECT ? ctx->block : STAGED_TILE; }
+
 void fill_tiles(lbm_ctx *ctx) {
     int tile = 0;
+    const int tc = tile_cells(ctx);
     for (auto &L : ctx->lat_h) {
         L.tile0 = tile;
-        tile += (L.n + ctx->block - 1) / ctx->block;
+        tile += (L.n + tc - 1) / tc;
     }
     ctx->ntiles = tile;
 }
@@ -138,7 +151,7 @@ int default_grid(lbm_ctx *ctx) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int nb = sweep_max_active_blocks(ctx->prec, 1, ctx->block);
+    int nb = sweep_max_active_blocks(ctx->prec, ctx->variant, ctx->block);
     if (nb <= 0) nb = 1;
     long long g = (long long)sms * nb;
     if (g > ctx->ntiles) g = ctx->ntiles;
@@ -203,7 +216,7 @@ lbm_status enqueue_step(lbm_ctx *ctx, bool timed) {
         }
         CK(cudaEventRecord(ctx->ev[ctx->ev_used], ctx->stream));
     }
-    CK(launch_sweep(ctx->prec, parity, sa, ctx->grid, ctx->block, ctx->stream));
+    CK(launch_sweep(ctx->prec, parity, ctx->variant, sa, ctx->grid, ctx->block, ctx->stream));
     if (timed) {
         CK(cudaEventRecord(ctx->ev[ctx->ev_used + 1], ctx->stream));
         ctx->ev_used += 2;
@@ -345,7 +358,10 @@ lbm_status create_common(const lbm_grid_desc *cells, int ncells, lbm_ctx **out) 
         L.ny = d.ny;
         L.nz = d.nz;
         L.n = d.nx * d.ny * d.nz;
-        L.npad = (L.n + 63) / 64 * 64;  // 256-byte aligned planes in every precision
+        // planes start on 64-element (>= 128-byte) boundaries; LBM_PLANE_PAD
+        // extra elements keep the 19 plane starts from sharing one DRAM
+        // channel pattern when n is a large power of two
+        L.npad = (L.n + 63) / 64 * 64 + LBM_PLANE_PAD;
         L.f_off = foff;
         L.c_off = coff;
         L.divx.init((uint32_t)d.nx);
@@ -361,15 +377,22 @@ lbm_status create_common(const lbm_grid_desc *cells, int ncells, lbm_ctx **out) 
             L.whi[a] = d.wall_u_hi[a];
             L.g[a] = d.body_force[a];
         }
+        for (int q = 0; q < Q; ++q) L.off[q] = cx(q) + cy(q) * d.nx + cz(q) * d.nx * d.ny;
         foff += (long long)Q * L.npad;
         coff += (L.n + 255) / 256 * 256;
+        // a shifted staging window reaches at most nx*ny + nx + 1 cells (plus one
+        // tile of slack) beyond its plane
+        const long long reach = (long long)d.nx * d.ny + d.nx + 1 + 2 * STAGED_TILE;
+        if (reach > ctx->guard) ctx->guard = reach;
     }
+    ctx->guard = (ctx->guard + 63) / 64 * 64;
     ctx->f_elems = foff;
     ctx->ncells = coff;
     fill_tiles(ctx);
 
     ctx->lat_d = (LatDev *)owned_alloc(ctx, sizeof(LatDev) * ncells);
-    ctx->f = owned_alloc(ctx, (size_t)foff * ctx->esize);
+    ctx->f_arena = owned_alloc(ctx, (size_t)(foff + 2 * ctx->guard) * ctx->esize);
+    ctx->f = ctx->f_arena ? (char *)ctx->f_arena + ctx->guard * ctx->esize : nullptr;
     ctx->flags = (uint8_t *)owned_alloc(ctx, (size_t)coff);
     ctx->pid = (uint32_t *)owned_alloc(ctx, (size_t)coff * 4);
     ctx->pid_prev = (uint32_t *)owned_alloc(ctx, (size_t)coff * 4);
@@ -387,7 +410,8 @@ lbm_status create_common(const lbm_grid_desc *cells, int ncells, lbm_ctx **out) 
         return s;
     }
     // fluid at rest: every stored offset f - w rho0 is zero
-    if (cudaMemsetAsync(ctx->f, 0, (size_t)foff * ctx->esize, ctx->stream) != cudaSuccess ||
+    if (cudaMemsetAsync(ctx->f_arena, 0, (size_t)(foff + 2 * ctx->guard) * ctx->esize, ctx->stream) !=
+            cudaSuccess ||
         cudaMemsetAsync(ctx->flags, 0, (size_t)coff, ctx->stream) != cudaSuccess ||
         cudaMemsetAsync(ctx->pid, 0xFF, (size_t)coff * 4, ctx->stream) != cudaSuccess ||
         cudaMemsetAsync(ctx->wall_acc, 0, sizeof(double) * 6 * ncells, ctx->stream) != cudaSuccess ||
@@ -797,16 +821,18 @@ lbm_status lbm_get_info(lbm_ctx *ctx, lbm_info *info) {
     info->steps_done = ctx->t;
     info->device_bytes = ctx->device_bytes;
     info->sweep_grid = ctx->grid;
-    info->sweep_block = ctx->block;
+    info->sweep_block = ctx->variant == SWEEP_RING ? 0 : (ctx->variant == SWEEP_STAGED ? -1 : ctx->block);
     info->bytes_per_population = ctx->esize;
     return LBM_OK;
 }
 
 lbm_status lbm_set_launch(lbm_ctx *ctx, int block, int grid) {
     if (!ctx) return LBM_ERR_ARG;
-    if (block < 32 || block > 256 || block % 32) return fail(ctx, LBM_ERR_ARG, "block must be a multiple of 32 in [32, 256]");
+    if (block != 0 && block != -1 && (block < 32 || block > 256 || block % 32))
+        return fail(ctx, LBM_ERR_ARG, "block must be 0 (ring sweep), -1 (staged sweep) or a multiple of 32 in [32, 256]");
     CK(cudaStreamSynchronize(ctx->stream));
-    ctx->block = block;
+    ctx->variant = block == 0 ? SWEEP_RING : (block == -1 ? SWEEP_STAGED : SWEEP_DIRECT);
+    ctx->block = block <= 0 ? STAGED_TILE : block;
     fill_tiles(ctx);
     lbm_status s = upload_lattices(ctx);
     if (s != LBM_OK) return s;
@@ -826,16 +852,20 @@ lbm_status lbm_autotune(lbm_ctx *ctx, int *block_out, int *grid_out) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int blocks[] = {128, 192, 256};
+    // candidates: the staged sweep (block 0) and the direct sweep at three
+    // block sizes, each with persistent grids (1x, 2x resident) and one tile
+    // per block
+    const int blocks[] = {0, -1, 128, 256};
     double best = 1e30;
-    int bb = ctx->block, bg = ctx->grid;
+    int bb = ctx->variant == SWEEP_RING ? 0 : (ctx->variant == SWEEP_STAGED ? -1 : ctx->block);
+    int bg = ctx->grid;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     for (int blk : blocks) {
         lbm_status s = lbm_set_launch(ctx, blk, 0);
         if (s != LBM_OK) break;
-        const int occ = sweep_max_active_blocks(ctx->prec, 1, blk);
+        const int occ = sweep_max_active_blocks(ctx->prec, ctx->variant, ctx->block);
         if (occ <= 0) continue;
         const int grids[] = {sms * occ, 2 * sms * occ, ctx->ntiles};
         for (int gr : grids) {
@@ -843,14 +873,14 @@ lbm_status lbm_autotune(lbm_ctx *ctx, int *block_out, int *grid_out) {
             ctx->grid = gr;
             SweepArgs sa = sweep_args(ctx);
             for (int w = 0; w < 2; ++w) {
-                launch_sweep(ctx->prec, 0, sa, gr, blk, ctx->stream);
-                launch_sweep(ctx->prec, 1, sa, gr, blk, ctx->stream);
+                CK(launch_sweep(ctx->prec, 0, ctx->variant, sa, gr, ctx->block, ctx->stream));
+                CK(launch_sweep(ctx->prec, 1, ctx->variant, sa, gr, ctx->block, ctx->stream));
             }
             CK(cudaEventRecord(e0, ctx->stream));
             const int reps = 4;
             for (int r = 0; r < reps; ++r) {
-                launch_sweep(ctx->prec, 0, sa, gr, blk, ctx->stream);
-                launch_sweep(ctx->prec, 1, sa, gr, blk, ctx->stream);
+                CK(launch_sweep(ctx->prec, 0, ctx->variant, sa, gr, ctx->block, ctx->stream));
+                CK(launch_sweep(ctx->prec, 1, ctx->variant, sa, gr, ctx->block, ctx->stream));
             }
             CK(cudaEventRecord(e1, ctx->stream));
             CK(cudaEventSynchronize(e1));

@@ -40,6 +40,11 @@ constexpr uint8_t F_NEAR = 1;     // fluid cell with at least one wall/obstacle 
 constexpr uint8_t F_SOLID = 2;    // wall or obstacle cell (not collided)
 constexpr uint8_t F_CHANGED = 4;  // touched by this step's re-mapping (transient)
 constexpr uint8_t F_WALL = 8;     // static wall layer (never re-mapped)
+// Fluid cells (with F_NEAR) whose wall/obstacle neighbours all belong to the
+// moving wall layer y = 0 (F_YLO) or y = ny-1 (F_YHI) of a non-periodic y
+// axis: their bounced directions are exactly those with c_y = -1 (resp. +1).
+constexpr uint8_t F_YLO = 16;
+constexpr uint8_t F_YHI = 32;
 
 constexpr uint32_t PID_FLUID = LBM_PID_FLUID;
 constexpr uint32_t PID_WALL_YLO = LBM_PID_WALL_YLO;
@@ -74,6 +79,7 @@ struct LatDev {
     int pad0;
     double omega, omega_odd, rho0;
     double wlo[3], whi[3], g[3];
+    int off[Q];            // linear offset of x + c_q for cells off the periodic faces
 };
 
 // Rigid bodies, structure of arrays, FP64 throughout.
@@ -130,14 +136,22 @@ template <> struct Store<LBM_BF16_OFFSET> {
     static __device__ __forceinline__ void st(T *p, C v) { *p = __float2bfloat16_rn(v); }
 };
 
+
 // Device error-word bits.
 constexpr uint32_t ERR_NONFINITE = 1u;
 constexpr uint32_t ERR_TIMEOUT = 2u;
 
 // --- launchers (defined in the .cu files) ---------------------------------
-cudaError_t launch_sweep(int prec, int parity, const SweepArgs &a, int grid, int block,
+// Sweep variants: direct (one cell per thread, `block` threads per block),
+// staged (tiles of 256 cells brought into shared memory by bulk asynchronous
+// copies) and ring (per-thread asynchronous prefetch ring, block 256).
+constexpr int SWEEP_DIRECT = 0;
+constexpr int SWEEP_STAGED = 1;
+constexpr int SWEEP_RING = 2;
+cudaError_t launch_sweep(int prec, int parity, int variant, const SweepArgs &a, int grid, int block,
                          cudaStream_t s);
-int sweep_max_active_blocks(int prec, int parity, int block);
+int sweep_max_active_blocks(int prec, int variant, int block);
+constexpr int STAGED_TILE = 256;
 
 struct RemapArgs {
     const LatDev *lat;

@@ -417,13 +417,26 @@ __device__ __forceinline__ uint8_t flag_of(const LatDev &L, const uint32_t *pid,
                                            int j, int k) {
     const uint32_t id = pid[coff + i + L.nx * (j + L.ny * k)];
     if (id != PID_FLUID) return id >= PID_WALL ? (F_SOLID | F_WALL) : F_SOLID;
-    uint8_t f = 0;
+    bool near = false, only_lo = true, only_hi = true;
 #pragma unroll
     for (int q = 1; q < Q; ++q) {
         const int n = lin(L, i + cx(q), j + cy(q), k + cz(q));
-        if (pid[coff + n] != PID_FLUID) f = F_NEAR;
+        const uint32_t nid = pid[coff + n];
+        if (nid != PID_FLUID) {
+            near = true;
+            // a wall cell hit along c_q must be in the layer c_q points to
+            only_lo = only_lo && nid == PID_WALL_YLO && cy(q) < 0;
+            only_hi = only_hi && nid == PID_WALL_YHI && cy(q) > 0;
+        } else {
+            // every direction into the layer must hit it: the layer is a full plane
+            only_lo = only_lo && !(cy(q) < 0 && j == 1 && !L.py);
+            only_hi = only_hi && !(cy(q) > 0 && j == L.ny - 2 && !L.py);
+        }
     }
-    return f;
+    if (!near) return 0;
+    if (only_lo && j == 1 && !L.py) return F_NEAR | F_YLO;
+    if (only_hi && j == L.ny - 2 && !L.py) return F_NEAR | F_YHI;
+    return F_NEAR;
 }
 
 __global__ void flags_region_kernel(RemapArgs a, int bpb) {
