@@ -194,6 +194,27 @@ lbm_status lbm_set_pdfs(lbm_ctx *ctx, int cell, const double *pdfs);
 lbm_status lbm_get_links(lbm_ctx *ctx, int cell, int32_t *idx, int8_t *q, uint32_t *pid, int cap,
                          int *count);
 
+/* Allocation-free form of the link compaction (the paper has no counterpart).
+ * Some callers cannot allocate device memory at the moment they need the link
+ * list: a solver embedded in a host application whose memory manager owns all
+ * device memory, or a latency-critical loop in which an allocation (which can
+ * synchronise the device) is not acceptable.  This call allocates nothing:
+ * the caller passes device buffers for the results and the per-block counts
+ * live in one fixed array in device memory that every GPU loading this library
+ * holds until the process exits (256 KiB).
+ *   d_idx, d_q, d_pid: device arrays of at least cap entries (may be NULL when
+ *     cap = 0); same content and order as lbm_get_links.
+ *   d_count: device int receiving the total number of links (may exceed cap).
+ * Asynchronous on the context's stream; nothing is copied to the host.
+ * Lattices above 16,777,216 cells (65,536 tiles of 256) are rejected with
+ * LBM_ERR_ARG.  The first call on a device looks up the device address of the
+ * fixed array for that device; make that first call before any stream capture.
+ * All calls share the array: calls whose work overlaps on the GPU (another
+ * stream, another context, another host thread) race on it and must be
+ * ordered by the caller. */
+lbm_status lbm_get_links_noalloc(lbm_ctx *ctx, int cell, int32_t *d_idx, int8_t *d_q, uint32_t *d_pid,
+                                 int cap, int *d_count);
+
 typedef struct lbm_info {
     long long ncells_total;     /* cells over all lattices */
     long long nfluid_hint;      /* not computed: -1 */

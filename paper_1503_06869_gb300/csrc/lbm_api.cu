@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -776,6 +777,66 @@ lbm_status lbm_set_pdfs(lbm_ctx *ctx, int cell, const double *pdfs) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     dfree(ctx, d);
     if (e != cudaSuccess) return fail(ctx, LBM_ERR_CUDA, std::string("set_pdfs: ") + cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Link compaction without device allocation.  The per-block link counts that
+// lbm_get_links keeps in freshly allocated scratch live here in one fixed
+// array in device memory, present on every GPU that loads this library until
+// the process exits.  Host code must not pass the array's name to a kernel:
+// on the host that name is only a stand-in, not a device address.  Its
+// device address is looked up once per device, with that device current.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int LINKS_NOALLOC_MAX_BLOCKS = 65536;  // 65536 tiles of 256 cells
+static __device__ __align__(256) int g_links_scratch[LINKS_NOALLOC_MAX_BLOCKS];
+
+constexpr int MAX_DEVICES = 64;
+std::mutex g_links_scratch_mu;
+int *g_links_scratch_addr[MAX_DEVICES] = {};
+
+// Device address of g_links_scratch on the current device (looked up on the
+// first call for that device).
+cudaError_t links_scratch_address(int **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_links_scratch_mu);
+    if (!g_links_scratch_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_links_scratch);
+        if (e != cudaSuccess) return e;
+        g_links_scratch_addr[dev] = static_cast<int *>(p);
+    }
+    *out = g_links_scratch_addr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_get_links_noalloc(lbm_ctx *ctx, int cell, int32_t *d_idx, int8_t *d_q, uint32_t *d_pid, int cap,
+                                 int *d_count) {
+    if (!ctx || !d_count || cap < 0) return LBM_ERR_ARG;
+    if (cell < 0 || cell >= ctx->nlat) return fail(ctx, LBM_ERR_ARG, "cell out of range");
+    const LatDev &h = ctx->lat_h[cell];
+    const int nblocks = (h.n + 255) / 256;
+    if (nblocks > LINKS_NOALLOC_MAX_BLOCKS)
+        return fail(ctx, LBM_ERR_ARG,
+                    "lattice larger than the allocation-free link scratch (at most 16777216 cells)");
+    int *scratch = nullptr;
+    CK(links_scratch_address(&scratch));
+    // every one of the nblocks entries is written by the count pass before the
+    // scan reads it, so nothing left by an earlier call needs clearing
+    CK(launch_links(h, ctx->lat_d + cell, ctx->flags, ctx->pid, scratch, nblocks, cap ? d_idx : nullptr,
+                    cap ? d_q : nullptr, cap ? d_pid : nullptr, cap, d_count, ctx->stream));
+    ctx->launches += 3;
     return LBM_OK;
 }
 

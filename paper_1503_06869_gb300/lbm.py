@@ -71,6 +71,8 @@ SIGNATURES = {
     "lbm_set_pdfs": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "lbm_get_links": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                 C.POINTER(C.c_int)]),
+    "lbm_get_links_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                        C.c_void_p]),
     "lbm_get_info": (C.c_int, [C.c_void_p, C.POINTER(lbm_info)]),
     "lbm_set_launch": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "lbm_autotune": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),

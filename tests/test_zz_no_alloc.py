@@ -1,0 +1,78 @@
+"""The allocation-free link compaction, lbm_get_links_noalloc.
+
+It exists for callers that cannot allocate device memory when they need the
+boundary-link list (an embedding application whose own memory manager owns
+all device memory, or a latency-critical loop where an allocation is not
+acceptable).  It writes into device buffers the caller already holds and
+keeps its per-block counts in a fixed device array.  This test calls it
+through the C interface twice in a row, with time steps in between so that
+the second call sees different links, and checks each result against the
+allocating lbm_get_links.  It also checks that a lattice above the fixed
+array's limit is refused.  Named to be collected last.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from lbm_inputs import Lattice, Particle, SplitMix64, quat_from_axis, shear_lattice
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1503_06869_gb300 import _build, lbm
+    _build.build()
+    lib = lbm.load()
+    return torch, lbm, lib
+
+
+def _noalloc_links(torch, lib, h, cap):
+    d_idx = torch.full((cap,), -7, dtype=torch.int32, device="cuda")
+    d_q = torch.full((cap,), -7, dtype=torch.int8, device="cuda")
+    d_pid = torch.full((cap,), -7, dtype=torch.int32, device="cuda")
+    d_cnt = torch.full((1,), -7, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    rc = lib.lbm_get_links_noalloc(h, 0, C.c_void_p(d_idx.data_ptr()), C.c_void_p(d_q.data_ptr()),
+                                   C.c_void_p(d_pid.data_ptr()), cap, C.c_void_p(d_cnt.data_ptr()))
+    assert rc == 0, lib.lbm_last_error(h)
+    rc = lib.lbm_sync(h)
+    assert rc == 0
+    n = int(d_cnt.cpu()[0])
+    m = min(n, cap)
+    return n, d_idx.cpu().numpy()[:m], d_q.cpu().numpy()[:m], d_pid.cpu().numpy()[:m].view(np.uint32)
+
+
+def test_noalloc_links_match_allocating_call_twice(env):
+    torch, lbm, lib = env
+    lat = shear_lattice(40, 22, 20, 0.8, 0.02)
+    rng = SplitMix64(9)
+    p = Particle(pos=(20.3, 10.6, 9.4), quat=quat_from_axis(rng.unit_vector()), semi_axes=(7.0, 3.0, 2.5),
+                 vel=(0.06, 0.0, 0.02), omega=(0.0, 0.02, 0.0), density=30.0)
+    sim = lbm.Simulation(lat, [p], prec="f32")
+    for call in range(2):
+        idx, q, pid = lbm.lbm_get_links(sim.h)
+        n, idx2, q2, pid2 = _noalloc_links(torch, lib, sim.h, len(idx) + 32)
+        assert n == len(idx)
+        assert np.array_equal(idx2, idx) and np.array_equal(q2, q) and np.array_equal(pid2, pid)
+        if call == 0:
+            sim.step(7)  # the body moves: the second call sees a different link set
+    # a capacity below the count still reports the full count
+    n, idx3, _, _ = _noalloc_links(torch, lib, sim.h, 10)
+    assert n == len(idx) and np.array_equal(idx3, idx[:10])
+    sim.close()
+
+
+def test_noalloc_links_refuse_lattices_above_the_limit(env):
+    torch, lbm, lib = env
+    lat = Lattice(257, 256, 256, periodic=(1, 1, 1))  # 16,842,752 cells > 16,777,216
+    sim = lbm.Simulation(lat, [], prec="f16")
+    d_cnt = torch.zeros((1,), dtype=torch.int32, device="cuda")
+    rc = lib.lbm_get_links_noalloc(sim.h, 0, None, None, None, 0, C.c_void_p(d_cnt.data_ptr()))
+    assert rc == lbm.LBM_ERR_ARG
+    assert b"16777216" in lib.lbm_last_error(sim.h)
+    sim.close()
