@@ -825,7 +825,7 @@ __global__ void __launch_bounds__(256, SweepBounds<PREC>::MINB)
     using C = typename S::C;
     using Cfg = RingCfg<PREC>;
     using Word = typename Cfg::Word;
-    extern __shared__ __align__(16) unsigned char dsm[];
+    extern __shared__ __align__(128) unsigned char dsm[];
     Word *ring = reinterpret_cast<Word *>(dsm);
     __shared__ Slots sh;
     __shared__ uint32_t tkey[256];
