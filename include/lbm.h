@@ -228,12 +228,16 @@ typedef struct lbm_info {
 
 lbm_status lbm_get_info(lbm_ctx *ctx, lbm_info *info);
 
-/* Sweep launch shape.  block = 0 selects the staged sweep (tiles of 256 cells
- * brought into shared memory by asynchronous bulk copies, several tiles in
- * flight per block); block = 32..256 (multiple of 32) selects the direct sweep
- * with that many threads, one cell each.  grid = number of blocks (<= 0: one
- * resident wave on every SM).  Used by the autotuner; takes effect at the next
- * lbm_step.  The default is the staged sweep. */
+/* Sweep launch shape.  block = 0 selects the ring sweep (256 threads, each
+ * keeping its next cells' populations in flight through asynchronous copies
+ * into shared memory); block = -1 selects the staged sweep (tiles of 256
+ * cells brought into shared memory by asynchronous bulk copies, several tiles
+ * in flight per block); block = 32..256 (multiple of 32) selects the direct
+ * sweep with that many threads, one cell each.  grid = number of blocks
+ * (<= 0: one block per tile for the direct sweep, one resident wave on every
+ * SM otherwise; capped at the tile count).  Used by the autotuner; takes
+ * effect at the next lbm_step.  Any other block value returns LBM_ERR_ARG.
+ * The default is the direct sweep with 128 threads. */
 lbm_status lbm_set_launch(lbm_ctx *ctx, int block, int grid);
 
 /* Choose the sweep launch shape by timing candidates on this context (runs

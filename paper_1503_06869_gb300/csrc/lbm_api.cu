@@ -47,8 +47,8 @@ struct lbm_ctx {
     long long guard = 0;            // guard band in elements on each side
 
     long long t = 0;
-    int variant = SWEEP_RING;       // sweep kernel variant
-    int block = 256, grid = 0, ntiles = 0;
+    int variant = SWEEP_DIRECT;     // sweep kernel variant
+    int block = 128, grid = 0, ntiles = 0;
     int remap_bpb = 8;
 
     bool graphs = true;
@@ -149,6 +149,7 @@ void fill_tiles(lbm_ctx *ctx) {
 }
 
 int default_grid(lbm_ctx *ctx) {
+    if (ctx->variant == SWEEP_DIRECT) return ctx->ntiles > 0 ? ctx->ntiles : 1;  // one tile per block
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -397,7 +398,7 @@ lbm_status create_common(const lbm_grid_desc *cells, int ncells, lbm_ctx **out) 
     ctx->flags = (uint8_t *)owned_alloc(ctx, (size_t)coff);
     ctx->pid = (uint32_t *)owned_alloc(ctx, (size_t)coff * 4);
     ctx->pid_prev = (uint32_t *)owned_alloc(ctx, (size_t)coff * 4);
-    ctx->wall_acc = (double *)owned_alloc(ctx, sizeof(double) * 6 * ncells);
+    ctx->wall_acc = (double *)owned_alloc(ctx, sizeof(double) * 6 * ACC_COPIES * ncells);
     ctx->wall_last = (double *)owned_alloc(ctx, sizeof(double) * 6 * ncells);
     ctx->err = (uint32_t *)owned_alloc(ctx, 16);
     if (!ctx->lat_d || !ctx->f || !ctx->flags || !ctx->pid || !ctx->pid_prev || !ctx->wall_acc ||
@@ -415,7 +416,7 @@ lbm_status create_common(const lbm_grid_desc *cells, int ncells, lbm_ctx **out) 
             cudaSuccess ||
         cudaMemsetAsync(ctx->flags, 0, (size_t)coff, ctx->stream) != cudaSuccess ||
         cudaMemsetAsync(ctx->pid, 0xFF, (size_t)coff * 4, ctx->stream) != cudaSuccess ||
-        cudaMemsetAsync(ctx->wall_acc, 0, sizeof(double) * 6 * ncells, ctx->stream) != cudaSuccess ||
+        cudaMemsetAsync(ctx->wall_acc, 0, sizeof(double) * 6 * ACC_COPIES * ncells, ctx->stream) != cudaSuccess ||
         cudaMemsetAsync(ctx->wall_last, 0, sizeof(double) * 6 * ncells, ctx->stream) != cudaSuccess ||
         cudaMemsetAsync(ctx->err, 0, 16, ctx->stream) != cudaSuccess) {
         lbm_destroy(ctx);
@@ -429,11 +430,11 @@ lbm_status create_common(const lbm_grid_desc *cells, int ncells, lbm_ctx **out) 
         }
         ctx->launches += 2;
     }
+    ctx->grid = default_grid(ctx);
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
         lbm_destroy(ctx);
         return LBM_ERR_CUDA;
     }
-    ctx->grid = default_grid(ctx);
     *out = ctx;
     return LBM_OK;
 }
@@ -479,7 +480,8 @@ lbm_status lbm_set_particles(lbm_ctx *ctx, const lbm_particle *p, int n) {
     if (n < 0 || (n > 0 && !p)) return fail(ctx, LBM_ERR_ARG, "bad particle array");
     // validate and derive host-side quantities
     std::vector<double> pos(3 * n), quat(4 * n), vel(3 * n), om(3 * n), L(3 * n), semi(3 * n), mass(n),
-        inertia(3 * n), extF(3 * n), extM(3 * n);
+        inertia(3 * n), extF(3 * n), extM(3 * n), minv(n), Iinv(3 * n);
+    std::vector<float> bodyf(16 * (size_t)n, 0.0f);
     std::vector<int> cell(n), fixed(n), region(6 * n);
     for (int i = 0; i < n; ++i) {
         const lbm_particle &b = p[i];
@@ -535,6 +537,11 @@ lbm_status lbm_set_particles(lbm_ctx *ctx, const lbm_particle *p, int n) {
         }
         for (int k = 0; k < 4; ++k) quat[4 * i + k] = q[k];
         mass[i] = m;
+        minv[i] = 1.0 / m;
+        for (int a = 0; a < 3; ++a) Iinv[3 * i + a] = 1.0 / I[a];
+        for (int k = 0; k < 9; ++k) bodyf[16 * i + k] = (float)R[k];
+        for (int a = 0; a < 3; ++a) bodyf[16 * i + 9 + a] = (float)(1.0 / b.semi_axes[a]);
+        for (int a = 0; a < 3; ++a) bodyf[16 * i + 12 + a] = (float)b.pos[a];
         cell[i] = b.cell;
         fixed[i] = b.fixed ? 1 : 0;
     }
@@ -569,6 +576,9 @@ lbm_status lbm_set_particles(lbm_ctx *ctx, const lbm_particle *p, int n) {
     P.semi = part_alloc<double>(ctx, 3 * m);
     P.mass = part_alloc<double>(ctx, m);
     P.inertia = part_alloc<double>(ctx, 3 * m);
+    P.minv = part_alloc<double>(ctx, m);
+    P.Iinv = part_alloc<double>(ctx, 3 * m);
+    P.bodyf = part_alloc<float>(ctx, 16 * m);
     P.extF = part_alloc<double>(ctx, 3 * m);
     P.extM = part_alloc<double>(ctx, 3 * m);
     P.cell = part_alloc<int>(ctx, m);
@@ -577,7 +587,7 @@ lbm_status lbm_set_particles(lbm_ctx *ctx, const lbm_particle *p, int n) {
     P.vel_old = part_alloc<double>(ctx, 3 * m);
     P.om_old = part_alloc<double>(ctx, 3 * m);
     P.quat_old = part_alloc<double>(ctx, 4 * m);
-    P.acc = part_alloc<double>(ctx, 6 * m);
+    P.acc = part_alloc<double>(ctx, 6 * ACC_COPIES * m);
     P.last = part_alloc<double>(ctx, 6 * m);
     P.region = part_alloc<int>(ctx, 6 * m);
     for (void *b : ctx->part_bufs)
@@ -598,6 +608,9 @@ lbm_status lbm_set_particles(lbm_ctx *ctx, const lbm_particle *p, int n) {
     CK(up(P.semi, semi.data(), 8 * semi.size()));
     CK(up(P.mass, mass.data(), 8 * mass.size()));
     CK(up(P.inertia, inertia.data(), 8 * inertia.size()));
+    CK(up(P.minv, minv.data(), 8 * minv.size()));
+    CK(up(P.Iinv, Iinv.data(), 8 * Iinv.size()));
+    CK(up(P.bodyf, bodyf.data(), 4 * bodyf.size()));
     CK(up(P.extF, extF.data(), 8 * extF.size()));
     CK(up(P.extM, extM.data(), 8 * extM.size()));
     CK(up(P.cell, cell.data(), 4 * cell.size()));
@@ -607,7 +620,7 @@ lbm_status lbm_set_particles(lbm_ctx *ctx, const lbm_particle *p, int n) {
     CK(up(P.om_old, om.data(), 8 * om.size()));
     CK(up(P.quat_old, quat.data(), 8 * quat.size()));
     CK(up(P.region, region.data(), 4 * region.size()));
-    CK(cudaMemsetAsync(P.acc, 0, sizeof(double) * 6 * m, ctx->stream));
+    CK(cudaMemsetAsync(P.acc, 0, sizeof(double) * 6 * ACC_COPIES * m, ctx->stream));
     CK(cudaMemsetAsync(P.last, 0, sizeof(double) * 6 * m, ctx->stream));
     // full re-map of every lattice for the next sweep's parity
     RemapArgs ra = remap_args(ctx);
@@ -638,7 +651,7 @@ lbm_status lbm_step(lbm_ctx *ctx, int nsteps) {
                 lbm_status s = build_graph(ctx);
                 if (s != LBM_OK) return s;
             }
-            const int per = 2 + 2 * (ctx->np > 0 ? kernels_per_remap_step() : 0);
+            const int per = 2 * (2 + (ctx->np > 0 ? kernels_per_remap_step() : 0));
             while (left >= 2) {
                 CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
                 ctx->t += 2;
@@ -899,6 +912,7 @@ lbm_status lbm_set_launch(lbm_ctx *ctx, int block, int grid) {
     if (s != LBM_OK) return s;
     ctx->grid = grid > 0 ? (grid < ctx->ntiles ? grid : ctx->ntiles) : default_grid(ctx);
     drop_graph(ctx);
+    CK(cudaStreamSynchronize(ctx->stream));
     return LBM_OK;
 }
 
@@ -913,9 +927,9 @@ lbm_status lbm_autotune(lbm_ctx *ctx, int *block_out, int *grid_out) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // candidates: the staged sweep (block 0) and the direct sweep at three
-    // block sizes, each with persistent grids (1x, 2x resident) and one tile
-    // per block
+    // candidates: the ring sweep (block 0), the staged sweep (block -1) and
+    // the direct sweep at two block sizes, each with persistent grids (1x, 2x
+    // resident) and one tile per block
     const int blocks[] = {0, -1, 128, 256};
     double best = 1e30;
     int bb = ctx->variant == SWEEP_RING ? 0 : (ctx->variant == SWEEP_STAGED ? -1 : ctx->block);
@@ -959,8 +973,8 @@ lbm_status lbm_autotune(lbm_ctx *ctx, int *block_out, int *grid_out) {
     cudaEventDestroy(e1);
     lbm_status s = lbm_set_launch(ctx, bb, bg);
     CK(cudaMemcpyAsync(ctx->f, backup, fbytes, cudaMemcpyDeviceToDevice, ctx->stream));
-    if (ctx->np > 0) CK(cudaMemsetAsync(ctx->P.acc, 0, sizeof(double) * 6 * ctx->np, ctx->stream));
-    CK(cudaMemsetAsync(ctx->wall_acc, 0, sizeof(double) * 6 * ctx->nlat, ctx->stream));
+    if (ctx->np > 0) CK(cudaMemsetAsync(ctx->P.acc, 0, sizeof(double) * 6 * ACC_COPIES * ctx->np, ctx->stream));
+    CK(cudaMemsetAsync(ctx->wall_acc, 0, sizeof(double) * 6 * ACC_COPIES * ctx->nlat, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     dfree(ctx, backup);
     if (block_out) *block_out = bb;

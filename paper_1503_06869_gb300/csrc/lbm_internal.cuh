@@ -88,6 +88,8 @@ struct PartDev {
     int pad0;
     double *pos, *quat, *vel, *om, *L;   // current state (3/4/3/3/3 per body)
     double *semi, *mass, *inertia;       // shape: semi-axes, mass, body inertia diag
+    double *minv, *Iinv;                 // 1/mass, 1/inertia (host-computed)
+    float *bodyf;                        // 16 per body: FP32 rotation, 1/semi-axes, centre
     double *extF, *extM;                 // external loads
     int *cell, *fixed;
     double *pos_old, *vel_old, *om_old, *quat_old; // state before this step's update
@@ -136,6 +138,13 @@ template <> struct Store<LBM_BF16_OFFSET> {
     static __device__ __forceinline__ void st(T *p, C v) { *p = __float2bfloat16_rn(v); }
 };
 
+
+// Force/torque accumulators are kept in ACC_COPIES copies per body (and per
+// lattice wall pair); a warp adds into copy (8*block + warp) mod ACC_COPIES,
+// which spreads same-address FP64 atomics, and the rigid-body kernel sums the
+// copies.  Layout: body p, copy c -> acc[(p*ACC_COPIES + c)*6 + k] (F then M);
+// lattice l, copy c -> wall_acc[(l*ACC_COPIES + c)*6 + 3*side + k].
+constexpr int ACC_COPIES = 32;
 
 // Device error-word bits.
 constexpr uint32_t ERR_NONFINITE = 1u;

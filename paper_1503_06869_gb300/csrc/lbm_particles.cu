@@ -81,27 +81,52 @@ __device__ __forceinline__ bool inside_rn(const LatDev &L, const double *pos, co
 // box (|d| below ~10^2, semi-axes >= ~1), so outside a band |s - 1| <= 1e-3
 // the FP32 decision equals the FP64 one, and inside the band the exact FP64
 // test decides.  The result is bit-identical to inside_rn.
+// FP32 copy of a body's pose for that pre-test (kept per body in
+// PartDev::bodyf: rotation, reciprocal semi-axes, centre).
 struct BodyF32 {
     float R[9];
     float inv[3];
+    float pos[3];
 };
 
-__device__ __forceinline__ void body_f32(const double R[9], const double *semi, BodyF32 &b) {
-    for (int k = 0; k < 9; ++k) b.R[k] = (float)R[k];
-    for (int k = 0; k < 3; ++k) b.inv[k] = (float)(1.0 / semi[k]);
+__device__ __forceinline__ void load_body_f32(const float *src, BodyF32 &b) {
+    for (int k = 0; k < 9; ++k) b.R[k] = src[k];
+    for (int k = 0; k < 3; ++k) b.inv[k] = src[9 + k];
+    for (int k = 0; k < 3; ++k) b.pos[k] = src[12 + k];
 }
 
-__device__ __forceinline__ bool inside_fast(const LatDev &L, const double *pos, const double R[9],
+__device__ __forceinline__ float min_image_f(float d, int n, int periodic, bool &near_switch) {
+    if (periodic) {
+        const float h = 0.5f * (float)n;
+        near_switch = near_switch || fabsf(fabsf(d) - h) < 2.0f;
+        if (d > h)
+            d -= (float)n;
+        else if (d < -h)
+            d += (float)n;
+    }
+    return d;
+}
+
+// Exact inside test of the cell (i,j,k) for the body with double pose
+// (pos, quat), decided in FP32 where the FP32 value of s is far from 1; cells
+// near the periodic image switch (|d| ~ n/2) always take the FP64 test.
+__device__ __forceinline__ bool inside_fast(const LatDev &L, const double *pos, const double *quat,
                                             const double *semi, const BodyF32 &b, int i, int j, int k) {
-    const float d0 = (float)min_image_rn((double)i - pos[0], L.nx, L.px);
-    const float d1 = (float)min_image_rn((double)j - pos[1], L.ny, L.py);
-    const float d2 = (float)min_image_rn((double)k - pos[2], L.nz, L.pz);
+    // d in FP64 then rounded once: |error(s)| < ~2e-4 for |d| < 100, semi-axes >= 1
+    bool sw = false;
+    const float d0 = min_image_f((float)((double)i - pos[0]), L.nx, L.px, sw);
+    const float d1 = min_image_f((float)((double)j - pos[1]), L.ny, L.py, sw);
+    const float d2 = min_image_f((float)((double)k - pos[2]), L.nz, L.pz, sw);
     const float t0 = (b.R[0] * d0 + b.R[3] * d1 + b.R[6] * d2) * b.inv[0];
     const float t1 = (b.R[1] * d0 + b.R[4] * d1 + b.R[7] * d2) * b.inv[1];
     const float t2 = (b.R[2] * d0 + b.R[5] * d1 + b.R[8] * d2) * b.inv[2];
     const float s = t0 * t0 + t1 * t1 + t2 * t2;
-    if (s < 0.999f) return true;
-    if (s > 1.001f) return false;
+    if (!sw) {
+        if (s < 0.999f) return true;
+        if (s > 1.001f) return false;
+    }
+    double R[9];
+    quat_matrix_rn(quat, R);
     return inside_rn(L, pos, R, semi, i, j, k);
 }
 
@@ -117,30 +142,58 @@ __device__ __forceinline__ void aabb_half(const double R[9], const double *semi,
 // rigid-body update (one thread per body) and wall-force hand-over
 // ---------------------------------------------------------------------------
 
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// One warp per body (and per lattice for the wall loads): lane c reads and
+// clears accumulator copy c, the warp sums the copies, and lane 0 runs the
+// body's update (Sec. 4.3) on register copies of its state: every load is
+// issued up front, every store at the end, so the FP64 chain pays one memory
+// round trip instead of one per dependent access.
 __global__ void rigid_body_kernel(RemapArgs a) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    static_assert(ACC_COPIES == 32, "one lane per accumulator copy");
+    const int t = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
     if (t < a.nlat) {
-        for (int k = 0; k < 6; ++k) {
-            a.wall_last[6 * t + k] = a.wall_acc[6 * t + k];
-            a.wall_acc[6 * t + k] = 0.0;
-        }
+        double *w = a.wall_acc + 6 * ((size_t)t * ACC_COPIES + lane);
+        double s[6];
+        for (int k = 0; k < 6; ++k) s[k] = w[k];
+        for (int k = 0; k < 6; ++k) w[k] = 0.0;
+        for (int k = 0; k < 6; ++k) s[k] = warp_sum(s[k]);
+        if (lane == 0)
+            for (int k = 0; k < 6; ++k) a.wall_last[6 * t + k] = s[k];
     }
     const PartDev &P = a.P;
     if (t >= P.np) return;
-    double *acc = P.acc + 6 * t, *last = P.last + 6 * t;
-    double F[3], M[3];
-    bool finite = true;
-    for (int k = 0; k < 3; ++k) {
-        last[k] = acc[k];
-        last[3 + k] = acc[3 + k];
-        F[k] = acc[k] + P.extF[3 * t + k];
-        M[k] = acc[3 + k] + P.extM[3 * t + k];
-        acc[k] = 0.0;
-        acc[3 + k] = 0.0;
-        finite = finite && isfinite(F[k]) && isfinite(M[k]);
+    double hs[6];  // F_h, M_h: the sweep's copies, summed
+    {
+        double *acc = P.acc + 6 * ((size_t)t * ACC_COPIES + lane);
+        for (int k = 0; k < 6; ++k) hs[k] = acc[k];
+        for (int k = 0; k < 6; ++k) acc[k] = 0.0;
+        for (int k = 0; k < 6; ++k) hs[k] = warp_sum(hs[k]);
     }
-    double *pos = P.pos + 3 * t, *vel = P.vel + 3 * t, *om = P.om + 3 * t, *L = P.L + 3 * t;
-    double *q = P.quat + 4 * t;
+    if (lane != 0) return;
+
+    double pos[3], vel[3], om[3], Lm[3], q[4], semi[3], Iinv[3], eF[3], eM[3];
+    for (int k = 0; k < 3; ++k) {
+        pos[k] = P.pos[3 * t + k];
+        vel[k] = P.vel[3 * t + k];
+        om[k] = P.om[3 * t + k];
+        Lm[k] = P.L[3 * t + k];
+        semi[k] = P.semi[3 * t + k];
+        Iinv[k] = P.Iinv[3 * t + k];
+        eF[k] = P.extF[3 * t + k];
+        eM[k] = P.extM[3 * t + k];
+    }
+    for (int k = 0; k < 4; ++k) q[k] = P.quat[4 * t + k];
+    const double minv = P.minv[t];
+    const int fixed = P.fixed[t];
+    const LatDev &Lt = a.lat[P.cell[t]];
+    const int dims[3] = {Lt.nx, Lt.ny, Lt.nz}, per[3] = {Lt.px, Lt.py, Lt.pz};
+
+    for (int k = 0; k < 6; ++k) P.last[6 * t + k] = hs[k];
     for (int k = 0; k < 3; ++k) {
         P.pos_old[3 * t + k] = pos[k];
         P.vel_old[3 * t + k] = vel[k];
@@ -148,44 +201,52 @@ __global__ void rigid_body_kernel(RemapArgs a) {
     }
     for (int k = 0; k < 4; ++k) P.quat_old[4 * t + k] = q[k];
 
-    const LatDev &Lt = a.lat[P.cell[t]];
+    double F[3], M[3];
+    bool finite = true;
+    for (int k = 0; k < 3; ++k) {
+        F[k] = hs[k] + eF[k];
+        M[k] = hs[3 + k] + eM[k];
+        finite = finite && isfinite(F[k]) && isfinite(M[k]);
+    }
     double Rold[9];
     quat_matrix_rn(q, Rold);
-    const double *semi = P.semi + 3 * t;
     double hold[3], cold[3] = {pos[0], pos[1], pos[2]};
     aabb_half(Rold, semi, hold);
 
-    if (!P.fixed[t]) {
-        const double m = P.mass[t];
-        const double *I = P.inertia + 3 * t;
-        for (int k = 0; k < 3; ++k) vel[k] += F[k] / m;
+    if (!fixed) {
+        // divisions are replaced by the host's reciprocals of mass and inertia
+        for (int k = 0; k < 3; ++k) vel[k] += F[k] * minv;
         for (int k = 0; k < 3; ++k) pos[k] += vel[k];
-        for (int k = 0; k < 3; ++k) L[k] += M[k];
+        for (int k = 0; k < 3; ++k) Lm[k] += M[k];
         // omega = R diag(1/I) R^T L with the orientation before the update
         double lb[3];
         for (int k = 0; k < 3; ++k)
-            lb[k] = (Rold[k] * L[0] + Rold[3 + k] * L[1] + Rold[6 + k] * L[2]) / I[k];
+            lb[k] = (Rold[k] * Lm[0] + Rold[3 + k] * Lm[1] + Rold[6 + k] * Lm[2]) * Iinv[k];
         for (int k = 0; k < 3; ++k)
             om[k] = Rold[3 * k] * lb[0] + Rold[3 * k + 1] * lb[1] + Rold[3 * k + 2] * lb[2];
-        const double th = sqrt(om[0] * om[0] + om[1] * om[1] + om[2] * om[2]);
-        double dq[4] = {1.0, 0.0, 0.0, 0.0};
-        if (th > 0.0) {
-            double sh, ch;
+        const double th2 = om[0] * om[0] + om[1] * om[1] + om[2] * om[2];
+        // exp(Omega/2) = (cos(th/2), sin(th/2) Omega/th); for the small angles of
+        // one lattice step the Maclaurin series of cos x and sin x / x in
+        // x^2 = th^2/4, truncated after x^8 (remainder < 1e-19 for th < 0.02)
+        double ch, shr;  // cos(th/2), sin(th/2)/th
+        if (th2 < 4e-4) {
+            const double x2 = 0.25 * th2;
+            ch = 1.0 + x2 * (-1.0 / 2 + x2 * (1.0 / 24 + x2 * (-1.0 / 720 + x2 * (1.0 / 40320))));
+            shr = 0.5 * (1.0 + x2 * (-1.0 / 6 + x2 * (1.0 / 120 + x2 * (-1.0 / 5040 + x2 * (1.0 / 362880)))));
+        } else {
+            const double th = sqrt(th2);
+            double sh;
             sincos(0.5 * th, &sh, &ch);
-            sh /= th;
-            dq[0] = ch;
-            dq[1] = om[0] * sh;
-            dq[2] = om[1] * sh;
-            dq[3] = om[2] * sh;
+            shr = sh / th;
         }
+        const double dq[4] = {ch, om[0] * shr, om[1] * shr, om[2] * shr};
         double nq[4];
         nq[0] = dq[0] * q[0] - (dq[1] * q[1] + dq[2] * q[2] + dq[3] * q[3]);
         nq[1] = dq[0] * q[1] + q[0] * dq[1] + (dq[2] * q[3] - dq[3] * q[2]);
         nq[2] = dq[0] * q[2] + q[0] * dq[2] + (dq[3] * q[1] - dq[1] * q[3]);
         nq[3] = dq[0] * q[3] + q[0] * dq[3] + (dq[1] * q[2] - dq[2] * q[1]);
-        const double nrm = sqrt(nq[0] * nq[0] + nq[1] * nq[1] + nq[2] * nq[2] + nq[3] * nq[3]);
-        for (int k = 0; k < 4; ++k) q[k] = nq[k] / nrm;
-        const int dims[3] = {Lt.nx, Lt.ny, Lt.nz}, per[3] = {Lt.px, Lt.py, Lt.pz};
+        const double rn = 1.0 / sqrt(nq[0] * nq[0] + nq[1] * nq[1] + nq[2] * nq[2] + nq[3] * nq[3]);
+        for (int k = 0; k < 4; ++k) q[k] = nq[k] * rn;
         for (int k = 0; k < 3; ++k)
             if (per[k]) {
                 if (pos[k] >= dims[k])
@@ -194,6 +255,13 @@ __global__ void rigid_body_kernel(RemapArgs a) {
                     pos[k] += dims[k];
             }
         for (int k = 0; k < 3; ++k) finite = finite && isfinite(pos[k]) && isfinite(om[k]);
+        for (int k = 0; k < 3; ++k) {
+            P.pos[3 * t + k] = pos[k];
+            P.vel[3 * t + k] = vel[k];
+            P.om[3 * t + k] = om[k];
+            P.L[3 * t + k] = Lm[k];
+        }
+        for (int k = 0; k < 4; ++k) P.quat[4 * t + k] = q[k];
     }
     if (!finite) atomicOr(a.err, ERR_NONFINITE);
 
@@ -201,7 +269,11 @@ __global__ void rigid_body_kernel(RemapArgs a) {
     double Rnew[9], hnew[3];
     quat_matrix_rn(q, Rnew);
     aabb_half(Rnew, semi, hnew);
-    const int dims[3] = {Lt.nx, Lt.ny, Lt.nz}, per[3] = {Lt.px, Lt.py, Lt.pz};
+    // FP32 copy of the new pose for the re-mapping pre-test (reciprocal
+    // semi-axes in bodyf[9..11] are set once, on the host)
+    float *bf = P.bodyf + 16 * t;
+    for (int k = 0; k < 9; ++k) bf[k] = (float)Rnew[k];
+    for (int k = 0; k < 3; ++k) bf[12 + k] = (float)pos[k];
     for (int k = 0; k < 3; ++k) {
         double lo = fmin(cold[k] - hold[k], pos[k] - hnew[k]);
         double hi = fmax(cold[k] + hold[k], pos[k] + hnew[k]);
@@ -271,23 +343,21 @@ __global__ void remap_region_kernel(RemapArgs a, int bpb) {
     const int vol = reg[3] * reg[4] * reg[5];
     if (vol <= 0) return;
     const LatDev &L = a.lat[P.cell[p]];
-    double R[9];
-    quat_matrix_rn(P.quat + 4 * p, R);
-    const double *pos = P.pos + 3 * p, *semi = P.semi + 3 * p;
+    const double *pos = P.pos + 3 * p, *semi = P.semi + 3 * p, *quat = P.quat + 4 * p;
     BodyF32 bf;
-    body_f32(R, semi, bf);
+    load_body_f32(P.bodyf + 16 * p, bf);
     for (int r = rl.first; r < vol; r += rl.stride) {
         RegionCell c;
         region_cell(reg, L, r, c);
         const long long cg = L.c_off + c.idx;
         if (PASS == 0) {  // uncover
-            if (a.pid[cg] == (uint32_t)p && !inside_fast(L, pos, R, semi, bf, c.i, c.j, c.k)) {
+            if (a.pid[cg] == (uint32_t)p && !inside_fast(L, pos, quat, semi, bf, c.i, c.j, c.k)) {
                 a.pid[cg] = PID_FLUID;
                 a.pid_prev[cg] = (uint32_t)p;
                 a.flags[cg] |= F_CHANGED;
             }
         } else {  // claim
-            if (!(a.flags[cg] & F_WALL) && inside_fast(L, pos, R, semi, bf, c.i, c.j, c.k)) {
+            if (!(a.flags[cg] & F_WALL) && inside_fast(L, pos, quat, semi, bf, c.i, c.j, c.k)) {
                 const uint32_t old = atomicMin(&a.pid[cg], (uint32_t)p);
                 if (old == PID_FLUID) a.flags[cg] |= F_CHANGED;
             }
@@ -452,7 +522,8 @@ __global__ void flags_region_kernel(RemapArgs a, int bpb) {
         region_cell(reg, L, r, c);
         const long long cg = L.c_off + c.idx;
         if (a.flags[cg] & F_WALL) continue;
-        a.flags[cg] = flag_of(L, a.pid, L.c_off, c.i, c.j, c.k);
+        const uint8_t f = flag_of(L, a.pid, L.c_off, c.i, c.j, c.k);
+        a.flags[cg] = f;
     }
 }
 
@@ -724,7 +795,7 @@ int kernels_per_remap_step() { return 4; }
 cudaError_t launch_rigid_body(const RemapArgs &a, cudaStream_t s) {
     const int n = a.P.np > a.nlat ? a.P.np : a.nlat;
     if (n <= 0) return cudaSuccess;
-    rigid_body_kernel<<<(n + 127) / 128, 128, 0, s>>>(a);
+    rigid_body_kernel<<<(int)((32ll * n + 127) / 128), 128, 0, s>>>(a);
     return cudaGetLastError();
 }
 

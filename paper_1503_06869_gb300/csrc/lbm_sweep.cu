@@ -51,11 +51,12 @@ struct Slots {
 };
 
 __device__ __forceinline__ double *global_acc(const SweepArgs &a, uint32_t key) {
+    const size_t c = (blockIdx.x * 8u + (threadIdx.x >> 5)) & (ACC_COPIES - 1);
     if (key & KEY_WALL) {
-        uint32_t l = (key & ~KEY_WALL) >> 1;
-        return a.wall_acc + 6 * (size_t)l + 3 * (key & 1u);
+        const size_t l = (key & ~KEY_WALL) >> 1;
+        return a.wall_acc + 6 * (l * ACC_COPIES + c) + 3 * (key & 1u);
     }
-    return a.P.acc + 6 * (size_t)key;
+    return a.P.acc + 6 * ((size_t)key * ACC_COPIES + c);
 }
 
 // Add a partial sum to the block table (or straight to global memory when
@@ -329,6 +330,33 @@ __device__ __noinline__ void near_cell(const SweepArgs &a, const LatDev &L, int 
             g[q] = S::ld(base + p * np + idx + nb_off(cg, p));
         }
     }
+    // Obstacle links: the ids of all obstacle neighbours are requested in one
+    // round trip; the first body met (p0) has its state loaded once and its
+    // links are bounced inline, in FP64, with the force and torque summed in
+    // registers; links to any further body take bounce_link.
+    const uint32_t obst = solid & ~wall;
+    uint32_t p0 = SLOT_EMPTY, m0 = 0;
+    if (obst) {
+        uint32_t ids[Q];
+#pragma unroll
+        for (int q = 1; q < Q; ++q)
+            ids[q] = ((obst >> q) & 1u) ? a.pid[L.c_off + idx + nb_off(cg, q)] : SLOT_EMPTY;
+#pragma unroll
+        for (int q = 1; q < Q; ++q)
+            if (ids[q] != SLOT_EMPTY) {
+                if (p0 == SLOT_EMPTY) p0 = ids[q];
+                if (ids[q] == p0) m0 |= 1u << q;
+            }
+    }
+    double bpos[3] = {0, 0, 0}, bU[3] = {0, 0, 0}, bW[3] = {0, 0, 0};
+    if (p0 != SLOT_EMPTY) {
+        for (int k = 0; k < 3; ++k) {
+            bpos[k] = a.P.pos[3 * (size_t)p0 + k];
+            bU[k] = a.P.vel[3 * (size_t)p0 + k];
+            bW[k] = a.P.om[3 * (size_t)p0 + k];
+        }
+    }
+    double bacc[6] = {0, 0, 0, 0, 0, 0};
     collide<C>(g, C(L.omega), C(L.omega_odd), C(L.rho0), C(L.g[0]), C(L.g[1]), C(L.g[2]));
     // Wall links are bounced inline in the compute precision: the wall layer
     // that is hit follows from the neighbour's y (a y = 0 or y = ny-1 layer
@@ -374,6 +402,27 @@ __device__ __noinline__ void near_cell(const SweepArgs &a, const LatDev &L, int 
                 if (cz(q)) { wsmall[2] += cz(q) > 0 ? ms : -ms; wconst[2] += cz(q) > 0 ? mc : -mc; }
             }
             S::st(base + opp(q) * np + idx, val);
+        } else if ((m0 >> q) & 1u) {
+            // velocity bounce-back off body p0 (Eq. LBMMovWall) and the link's
+            // momentum (2 f~ - 6 w rho0 c.u_s) c and torque (x_s - x_C) x dF
+            const double r0 = min_image((double)wrapc(cg.x + cx(q), L.nx) - bpos[0], L.nx, L.px);
+            const double r1 = min_image((double)wrapc(cg.y + cy(q), L.ny) - bpos[1], L.ny, L.py);
+            const double r2 = min_image((double)wrapc(cg.z + cz(q), L.nz) - bpos[2], L.nz, L.pz);
+            const double us0 = bU[0] + (bW[1] * r2 - bW[2] * r1);
+            const double us1 = bU[1] + (bW[2] * r0 - bW[0] * r2);
+            const double us2 = bU[2] + (bW[0] * r1 - bW[1] * r0);
+            const double cu = cx(q) * us0 + cy(q) * us1 + cz(q) * us2;
+            const double dbb = 6.0 * wq(q) * L.rho0 * cu;
+            const double ft = (double)g[q];
+            S::st(base + opp(q) * np + idx, (C)(ft - dbb));
+            const double mag = 2.0 * (ft + wq(q) * L.rho0) - dbb;
+            const double f0 = mag * cx(q), f1 = mag * cy(q), f2 = mag * cz(q);
+            bacc[0] += f0;
+            bacc[1] += f1;
+            bacc[2] += f2;
+            bacc[3] += r1 * f2 - r2 * f1;
+            bacc[4] += r2 * f0 - r0 * f2;
+            bacc[5] += r0 * f1 - r1 * f0;
         } else if ((solid >> q) & 1u) {
             const double v = bounce_link(a, L, li, q, idx + nb_off(cg, q), wrapc(cg.x + cx(q), L.nx),
                                          wrapc(cg.y + cy(q), L.ny), wrapc(cg.z + cz(q), L.nz),
@@ -385,6 +434,7 @@ __device__ __noinline__ void near_cell(const SweepArgs &a, const LatDev &L, int 
             S::st(base + q * np + idx + nb_off(cg, q), g[q]);
         }
     }
+    if (p0 != SLOT_EMPTY) tacc_add(a, tkey, tval, p0, bacc, 6);
     if (wside >= 0) {
         const uint32_t key = KEY_WALL | ((uint32_t)li << 1) | (uint32_t)wside;
         double v[3];
@@ -399,18 +449,24 @@ __device__ __noinline__ void near_cell(const SweepArgs &a, const LatDev &L, int 
 // bulk path's registers.  On odd steps the five populations arriving from the
 // layer are the ones the previous step bounced into slot q of x itself.
 template <int PREC, int ODD, int SIDE>
-__device__ __forceinline__ void wall_cell(const SweepArgs &a, const LatDev &L, int li, int idx,
-                                          const CellGeom &cg, typename Store<PREC>::C (&g)[Q],
+__device__ __noinline__ void wall_cell(const SweepArgs &a, const LatDev &L, int li, int idx,
                                           uint32_t *tkey, double *tval) {
     using S = Store<PREC>;
     using T = typename S::T;
     using C = typename S::C;
     T *base = reinterpret_cast<T *>(a.f) + L.f_off;
     const long long np = L.npad;
+    C g[Q];
+    CellGeom cg;
     if (ODD) {
+        cg = cell_geom(L, idx);
 #pragma unroll
-        for (int q = 1; q < Q; ++q)
-            if (SIDE == 0 ? cy(q) > 0 : cy(q) < 0) g[q] = S::ld(base + q * np + idx);
+        for (int q = 0; q < Q; ++q)
+            g[q] = (q != 0 && (SIDE == 0 ? cy(q) > 0 : cy(q) < 0)) ? S::ld(base + q * np + idx)
+                                                                  : S::ld(base + opp(q) * np + idx + nb_off(cg, opp(q)));
+    } else {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) g[q] = S::ld(base + q * np + idx);
     }
     collide<C>(g, C(L.omega), C(L.omega_odd), C(L.rho0), C(L.g[0]), C(L.g[1]), C(L.g[2]));
     const double *uw = SIDE == 0 ? L.wlo : L.whi;
@@ -499,6 +555,8 @@ __device__ __forceinline__ void flush_forces(const SweepArgs &a, Slots &, uint32
     }
 }
 
+// Direct sweep, one cell per thread: plain stream-collide for bulk cells,
+// the wall and near-obstacle paths for cells flagged F_YLO/F_YHI or F_NEAR.
 template <int PREC, int ODD, bool SINGLE>
 __global__ void __launch_bounds__(256, SweepBounds<PREC>::MINB)
     sweep_kernel(const __grid_constant__ SweepArgs a) {
@@ -515,11 +573,10 @@ __global__ void __launch_bounds__(256, SweepBounds<PREC>::MINB)
         const LatDev &L = SINGLE ? a.lat0 : a.lat[li];
         const int idx = (tile - L.tile0) * blockDim.x + threadIdx.x;
         if (idx >= L.n) continue;
-        // the flag byte and the 19 populations are requested together (one
-        // memory round trip per cell); the populations are read at the bulk
-        // pull addresses, which are in range for every cell
         T *base = reinterpret_cast<T *>(a.f) + L.f_off;
         const long long np = L.npad;
+        // the 19 populations are read at the bulk pull addresses, which are in
+        // range for every cell, in the same round trip as the flag byte
         C g[Q];
         CellGeom cg;
         if (ODD) {
@@ -534,12 +591,12 @@ __global__ void __launch_bounds__(256, SweepBounds<PREC>::MINB)
         if (fl & F_SOLID) continue;
         if (fl & (F_YLO | F_YHI)) {
             if (fl & F_YLO)
-                wall_cell<PREC, ODD, 0>(a, L, li, idx, cg, g, &tkey[threadIdx.x], tval[threadIdx.x]);
+                wall_cell<PREC, ODD, 0>(a, L, li, idx, &tkey[threadIdx.x], tval[threadIdx.x]);
             else
-                wall_cell<PREC, ODD, 1>(a, L, li, idx, cg, g, &tkey[threadIdx.x], tval[threadIdx.x]);
+                wall_cell<PREC, ODD, 1>(a, L, li, idx, &tkey[threadIdx.x], tval[threadIdx.x]);
             continue;
         }
-        if (fl & F_NEAR) {  // rare: reload from global memory inside the near path
+        if (fl & F_NEAR) {  // reload from global memory inside the near path
             near_cell<PREC, ODD, 0>(a, L, li, idx, &tkey[threadIdx.x], tval[threadIdx.x], &sh, nullptr);
             continue;
         }
