@@ -374,6 +374,10 @@ lbm_status create_common(const lbm_grid_desc *cells, int ncells, lbm_ctx **out) 
         L.omega = 1.0 / d.tau;
         L.omega_odd = 1.0 / (d.magic / (d.tau - 0.5) + 0.5);
         L.rho0 = d.rho0;
+        L.inv_rho0 = 1.0 / d.rho0;
+        L.rho18 = d.rho0 / 18.0;
+        L.rho18f[0] = (float)L.rho18;
+        L.rho18f[1] = (float)(L.rho18 - (double)L.rho18f[0]);
         for (int a = 0; a < 3; ++a) {
             L.wlo[a] = d.wall_u_lo[a];
             L.whi[a] = d.wall_u_hi[a];
@@ -481,7 +485,7 @@ lbm_status lbm_set_particles(lbm_ctx *ctx, const lbm_particle *p, int n) {
     // validate and derive host-side quantities
     std::vector<double> pos(3 * n), quat(4 * n), vel(3 * n), om(3 * n), L(3 * n), semi(3 * n), mass(n),
         inertia(3 * n), extF(3 * n), extM(3 * n), minv(n), Iinv(3 * n);
-    std::vector<float> bodyf(16 * (size_t)n, 0.0f);
+    std::vector<float> bodyf(BF_STRIDE * (size_t)n, 0.0f);
     std::vector<int> cell(n), fixed(n), region(6 * n);
     for (int i = 0; i < n; ++i) {
         const lbm_particle &b = p[i];
@@ -539,9 +543,15 @@ lbm_status lbm_set_particles(lbm_ctx *ctx, const lbm_particle *p, int n) {
         mass[i] = m;
         minv[i] = 1.0 / m;
         for (int a = 0; a < 3; ++a) Iinv[3 * i + a] = 1.0 / I[a];
-        for (int k = 0; k < 9; ++k) bodyf[16 * i + k] = (float)R[k];
-        for (int a = 0; a < 3; ++a) bodyf[16 * i + 9 + a] = (float)(1.0 / b.semi_axes[a]);
-        for (int a = 0; a < 3; ++a) bodyf[16 * i + 12 + a] = (float)b.pos[a];
+        float *bf = &bodyf[BF_STRIDE * (size_t)i];
+        for (int k = 0; k < 9; ++k) bf[BF_R + k] = (float)R[k];
+        for (int a = 0; a < 3; ++a) {
+            bf[BF_INV + a] = (float)(1.0 / b.semi_axes[a]);
+            bf[BF_POS + a] = (float)b.pos[a];
+            bf[BF_POSLO + a] = (float)(b.pos[a] - (double)bf[BF_POS + a]);
+            bf[BF_U + a] = (float)b.vel[a];
+            bf[BF_W + a] = (float)b.omega[a];
+        }
         cell[i] = b.cell;
         fixed[i] = b.fixed ? 1 : 0;
     }
@@ -578,7 +588,7 @@ lbm_status lbm_set_particles(lbm_ctx *ctx, const lbm_particle *p, int n) {
     P.inertia = part_alloc<double>(ctx, 3 * m);
     P.minv = part_alloc<double>(ctx, m);
     P.Iinv = part_alloc<double>(ctx, 3 * m);
-    P.bodyf = part_alloc<float>(ctx, 16 * m);
+    P.bodyf = part_alloc<float>(ctx, BF_STRIDE * m);
     P.extF = part_alloc<double>(ctx, 3 * m);
     P.extM = part_alloc<double>(ctx, 3 * m);
     P.cell = part_alloc<int>(ctx, m);

@@ -78,7 +78,10 @@ struct LatDev {
     int px, py, pz;        // periodic flags
     int pad0;
     double omega, omega_odd, rho0;
+    double inv_rho0;       // 1 / rho0
+    double rho18;          // rho0 / 18: 2 w_q rho0 = (36 w_q) rho0 / 18 with 36 w_q in {1, 2}
     double wlo[3], whi[3], g[3];
+    float rho18f[2];       // rho0 / 18 as a double-float (hi, lo)
     int off[Q];            // linear offset of x + c_q for cells off the periodic faces
 };
 
@@ -89,7 +92,7 @@ struct PartDev {
     double *pos, *quat, *vel, *om, *L;   // current state (3/4/3/3/3 per body)
     double *semi, *mass, *inertia;       // shape: semi-axes, mass, body inertia diag
     double *minv, *Iinv;                 // 1/mass, 1/inertia (host-computed)
-    float *bodyf;                        // 16 per body: FP32 rotation, 1/semi-axes, centre
+    float *bodyf;                        // BF_STRIDE per body, layout BF_* below
     double *extF, *extM;                 // external loads
     int *cell, *fixed;
     double *pos_old, *vel_old, *om_old, *quat_old; // state before this step's update
@@ -97,6 +100,12 @@ struct PartDev {
     double *last;      // 6 per body: F, M of the last completed step
     int *region;       // 6 per body: lo[3], ext[3] of the re-mapping box
 };
+
+// FP32 copy of a body's pose and motion (PartDev::bodyf, BF_STRIDE floats per
+// body): rotation matrix, reciprocal semi-axes, centre as a double-float
+// (hi at BF_POS, lo at BF_POSLO), translational and angular velocity.
+constexpr int BF_STRIDE = 32;
+constexpr int BF_R = 0, BF_INV = 9, BF_POS = 12, BF_POSLO = 16, BF_U = 19, BF_W = 22;
 
 struct SweepArgs {
     LatDev lat0;             // copy of lattice 0 (used when nlat == 1)
@@ -145,6 +154,48 @@ template <> struct Store<LBM_BF16_OFFSET> {
 // copies.  Layout: body p, copy c -> acc[(p*ACC_COPIES + c)*6 + k] (F then M);
 // lattice l, copy c -> wall_acc[(l*ACC_COPIES + c)*6 + 3*side + k].
 constexpr int ACC_COPIES = 32;
+
+// Double-float numbers: the unevaluated sum hi + lo of two FP32 values
+// (about 48 significant bits), built from error-free transformations:
+// TwoSum (Knuth, TAOCP vol. 2, Sec. 4.2.2) and the FMA product error
+// (Ogita, Rump & Oishi 2005), renormalised as in Bailey's double-double
+// addition.  Every operation is an explicitly rounded FP32 intrinsic, so the
+// compiler neither contracts nor reorders them.
+struct df {
+    float hi, lo;
+};
+__device__ __forceinline__ df two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+    df s = two_sum(a.hi, b.hi);
+    const df t = two_sum(a.lo, b.lo);
+    s = two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+    return two_sum(s.hi, __fadd_rn(s.lo, t.lo));
+}
+__device__ __forceinline__ df df_add_f(df a, float b) {
+    const df s = two_sum(a.hi, b);
+    return two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ df df_mul(df a, df b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return two_sum(p, e);
+}
+__device__ __forceinline__ df df_mul_f(df a, float b) {
+    const float p = __fmul_rn(a.hi, b);
+    return two_sum(p, __fmaf_rn(a.lo, b, __fmaf_rn(a.hi, b, -p)));
+}
+__device__ __forceinline__ df df_from_double(double x) {
+    const float hi = __double2float_rn(x);
+    return {hi, __double2float_rn(x - (double)hi)};
+}
+__device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
 
 // Device error-word bits.
 constexpr uint32_t ERR_NONFINITE = 1u;

@@ -81,8 +81,8 @@ __device__ __forceinline__ bool inside_rn(const LatDev &L, const double *pos, co
 // box (|d| below ~10^2, semi-axes >= ~1), so outside a band |s - 1| <= 1e-3
 // the FP32 decision equals the FP64 one, and inside the band the exact FP64
 // test decides.  The result is bit-identical to inside_rn.
-// FP32 copy of a body's pose for that pre-test (kept per body in
-// PartDev::bodyf: rotation, reciprocal semi-axes, centre).
+// FP32 copy of a body's pose for that pre-test (from PartDev::bodyf:
+// rotation, reciprocal semi-axes, centre).
 struct BodyF32 {
     float R[9];
     float inv[3];
@@ -90,9 +90,9 @@ struct BodyF32 {
 };
 
 __device__ __forceinline__ void load_body_f32(const float *src, BodyF32 &b) {
-    for (int k = 0; k < 9; ++k) b.R[k] = src[k];
-    for (int k = 0; k < 3; ++k) b.inv[k] = src[9 + k];
-    for (int k = 0; k < 3; ++k) b.pos[k] = src[12 + k];
+    for (int k = 0; k < 9; ++k) b.R[k] = src[BF_R + k];
+    for (int k = 0; k < 3; ++k) b.inv[k] = src[BF_INV + k];
+    for (int k = 0; k < 3; ++k) b.pos[k] = src[BF_POS + k];
 }
 
 __device__ __forceinline__ float min_image_f(float d, int n, int periodic, bool &near_switch) {
@@ -269,11 +269,17 @@ __global__ void rigid_body_kernel(RemapArgs a) {
     double Rnew[9], hnew[3];
     quat_matrix_rn(q, Rnew);
     aabb_half(Rnew, semi, hnew);
-    // FP32 copy of the new pose for the re-mapping pre-test (reciprocal
-    // semi-axes in bodyf[9..11] are set once, on the host)
-    float *bf = P.bodyf + 16 * t;
-    for (int k = 0; k < 9; ++k) bf[k] = (float)Rnew[k];
-    for (int k = 0; k < 3; ++k) bf[12 + k] = (float)pos[k];
+    // FP32 copy of the new pose and motion for the re-mapping pre-test and
+    // the sweep's bounce-back (reciprocal semi-axes are set once, on the host)
+    float *bf = P.bodyf + BF_STRIDE * (size_t)t;
+    for (int k = 0; k < 9; ++k) bf[BF_R + k] = (float)Rnew[k];
+    for (int k = 0; k < 3; ++k) {
+        const df c = df_from_double(pos[k]);
+        bf[BF_POS + k] = c.hi;
+        bf[BF_POSLO + k] = c.lo;
+        bf[BF_U + k] = (float)vel[k];
+        bf[BF_W + k] = (float)om[k];
+    }
     for (int k = 0; k < 3; ++k) {
         double lo = fmin(cold[k] - hold[k], pos[k] - hnew[k]);
         double hi = fmax(cold[k] + hold[k], pos[k] + hnew[k]);
@@ -345,7 +351,7 @@ __global__ void remap_region_kernel(RemapArgs a, int bpb) {
     const LatDev &L = a.lat[P.cell[p]];
     const double *pos = P.pos + 3 * p, *semi = P.semi + 3 * p, *quat = P.quat + 4 * p;
     BodyF32 bf;
-    load_body_f32(P.bodyf + 16 * p, bf);
+    load_body_f32(P.bodyf + BF_STRIDE * (size_t)p, bf);
     for (int r = rl.first; r < vol; r += rl.stride) {
         RegionCell c;
         region_cell(reg, L, r, c);

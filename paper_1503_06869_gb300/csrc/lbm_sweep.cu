@@ -30,7 +30,6 @@ namespace lbm {
 
 namespace {
 
-constexpr int NSLOT = 32;
 constexpr uint32_t SLOT_EMPTY = 0xFFFFFFFFu;
 constexpr uint32_t KEY_WALL = 0x80000000u;
 
@@ -43,13 +42,6 @@ __constant__ double c_w[Q] = {1.0 / 3.0, 1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0, 1.0
                               1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0,
                               1.0 / 36.0};
 
-// Shared memory of a sweep block: a small hash table of per-body partial
-// sums, and one partial-sum entry per thread.
-struct Slots {
-    uint32_t key[NSLOT];
-    double v[NSLOT][6];
-};
-
 __device__ __forceinline__ double *global_acc(const SweepArgs &a, uint32_t key) {
     const size_t c = (blockIdx.x * 8u + (threadIdx.x >> 5)) & (ACC_COPIES - 1);
     if (key & KEY_WALL) {
@@ -57,23 +49,6 @@ __device__ __forceinline__ double *global_acc(const SweepArgs &a, uint32_t key) 
         return a.wall_acc + 6 * (l * ACC_COPIES + c) + 3 * (key & 1u);
     }
     return a.P.acc + 6 * ((size_t)key * ACC_COPIES + c);
-}
-
-// Add a partial sum to the block table (or straight to global memory when
-// the table is full).  Wall keys carry only a force.
-__device__ void slot_add(Slots *sh, const SweepArgs &a, uint32_t key, const double *v) {
-    const int nv = (key & KEY_WALL) ? 3 : 6;
-    const uint32_t h = (key * 2654435761u) % NSLOT;
-    for (int i = 0; i < NSLOT; ++i) {
-        const uint32_t s = (h + i) % NSLOT;
-        const uint32_t old = atomicCAS(&sh->key[s], SLOT_EMPTY, key);
-        if (old == SLOT_EMPTY || old == key) {
-            for (int k = 0; k < nv; ++k) atomicAdd(&sh->v[s][k], v[k]);
-            return;
-        }
-    }
-    double *g = global_acc(a, key);
-    for (int k = 0; k < nv; ++k) atomicAdd(g + k, v[k]);
 }
 
 __device__ __forceinline__ double min_image(double d, int n, int periodic) {
@@ -94,7 +69,7 @@ __device__ __forceinline__ int wrapc(int v, int n) { return v < 0 ? v + n : (v >
 // the odd one 3 w rho0 c.u (Eq. EqPDF_TRT with c_s^2 = 1/3); the body force
 // enters as the odd source 3 w rho0 c.g.
 template <class C>
-__device__ __forceinline__ void collide(C (&g)[Q], C om, C oo, C rho0, C gx, C gy, C gz) {
+__device__ __forceinline__ void collide(C (&g)[Q], C om, C oo, C rho0, C inv, C gx, C gy, C gz) {
     C dr = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
@@ -103,7 +78,6 @@ __device__ __forceinline__ void collide(C (&g)[Q], C om, C oo, C rho0, C gx, C g
         if (cy(q)) jy += cy(q) > 0 ? g[q] : -g[q];
         if (cz(q)) jz += cz(q) > 0 ? g[q] : -g[q];
     }
-    const C inv = C(1) / rho0;
     const C ux = jx * inv, uy = jy * inv, uz = jz * inv;
     const C base = dr - C(1.5) * rho0 * (ux * ux + uy * uy + uz * uz);
     g[0] = g[0] - om * (g[0] - C(wq(0)) * base);
@@ -171,32 +145,145 @@ __device__ __forceinline__ int tile_lattice(const SweepArgs &a, int tile) {
     return lo;
 }
 
+// Per-thread partial sums of force and torque.  FP64 lattices keep them in
+// FP64.  The FP32/FP16/BF16 lattices keep them as double-floats: GB300 issues
+// FP64 arithmetic at a small fraction of its FP32 rate, and a single lane's
+// FP64 chain on the sweep's critical path stalls the whole sweep, so the
+// partials are compensated FP32 sums (about 48 significant bits) and only the
+// global accumulators are FP64.
+template <int PREC> struct Acc {
+    using V = df;
+    static __device__ __forceinline__ V zero() { return {0.f, 0.f}; }
+    static __device__ __forceinline__ V add(V x, V y) { return df_add(x, y); }
+    static __device__ __forceinline__ V sub(V x, V y) { return df_add(x, df_neg(y)); }
+    static __device__ __forceinline__ V mul(V x, V y) { return df_mul(x, y); }
+    static __device__ __forceinline__ V from(double x) { return df_from_double(x); }
+    static __device__ __forceinline__ double to_double(V x) { return df_to_double(x); }
+    static __device__ __forceinline__ V shfl_xor(V x, int o) {
+        return {__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o)};
+    }
+};
+template <> struct Acc<LBM_F64> {
+    using V = double;
+    static __device__ __forceinline__ V zero() { return 0.0; }
+    static __device__ __forceinline__ V add(V x, V y) { return x + y; }
+    static __device__ __forceinline__ V sub(V x, V y) { return x - y; }
+    static __device__ __forceinline__ V mul(V x, V y) { return x * y; }
+    static __device__ __forceinline__ V from(double x) { return x; }
+    static __device__ __forceinline__ double to_double(V x) { return x; }
+    static __device__ __forceinline__ V shfl_xor(V x, int o) { return __shfl_xor_sync(0xffffffffu, x, o); }
+};
+
 // Add nv components to this thread's partial sum for `key` (a body or a
 // wall).  A thread holds one key at a time; meeting another key first hands
 // the held partial to the global accumulators.
-__device__ __forceinline__ void tacc_add(const SweepArgs &a, uint32_t *tkey, double *tval, uint32_t key,
-                                         const double *v, int nv) {
+template <int PREC>
+__device__ __forceinline__ void tacc_add(const SweepArgs &a, uint32_t *tkey, typename Acc<PREC>::V *tval,
+                                         uint32_t key, const typename Acc<PREC>::V *v, int nv) {
+    using A = Acc<PREC>;
     if (*tkey != key) {
         if (*tkey != SLOT_EMPTY) {
             double *g = global_acc(a, *tkey);
             const int nk = (*tkey & KEY_WALL) ? 3 : 6;
-            for (int k = 0; k < nk; ++k) atomicAdd(g + k, tval[k]);
+            for (int k = 0; k < nk; ++k) atomicAdd(g + k, A::to_double(tval[k]));
         }
         *tkey = key;
-        for (int k = 0; k < 6; ++k) tval[k] = 0.0;
+        for (int k = 0; k < 6; ++k) tval[k] = A::zero();
     }
-    for (int k = 0; k < nv; ++k) tval[k] += v[k];
+    for (int k = 0; k < nv; ++k) tval[k] = A::add(tval[k], v[k]);
+}
+
+// Momentum handed over by the links of one cell to one body or wall
+// (Eq. TransferredMomentum): the link momentum (2 f~_q - 6 w_q rho0 c_q.u_s) c_q
+// is split into the small part (2 g~_q - 6 w_q rho0 c_q.u_s) c_q, g~ the stored
+// post-collision offset, summed with compensation in the compute precision,
+// and the constant part 2 w_q rho0 c_q = (rho0/18) (36 w_q) c_q, counted
+// exactly as the integer vector sum of (36 w_q) c_q.
+template <class C> struct LinkSum {
+    C s[3] = {0, 0, 0}, e[3] = {0, 0, 0};
+    int n[3] = {0, 0, 0};
+    __device__ __forceinline__ void add(int k, C v) {
+        if constexpr (sizeof(C) == 4) {
+            const df t = two_sum(s[k], v);
+            s[k] = t.hi;
+            e[k] = __fadd_rn(e[k], t.lo);
+        } else {
+            s[k] += v;
+        }
+    }
+    // link q (an unrolled loop index, so the branches fold) with small part sm
+    __device__ __forceinline__ void link(int q, C sm) {
+        const int w36 = q <= 6 ? 2 : 1;
+        if (cx(q)) { add(0, cx(q) > 0 ? sm : -sm); n[0] += cx(q) * w36; }
+        if (cy(q)) { add(1, cy(q) > 0 ? sm : -sm); n[1] += cy(q) * w36; }
+        if (cz(q)) { add(2, cz(q) > 0 ? sm : -sm); n[2] += cz(q) * w36; }
+    }
+};
+
+// Total momentum of a LinkSum: F_k = small_k + (rho0/18) n_k.
+template <int PREC, class C>
+__device__ __forceinline__ void link_force(const LatDev &L, const LinkSum<C> &ls, typename Acc<PREC>::V F[3]) {
+    if constexpr (PREC == LBM_F64) {
+        for (int k = 0; k < 3; ++k) F[k] = ls.s[k] + L.rho18 * (double)ls.n[k];
+    } else {
+        const df r18 = {L.rho18f[0], L.rho18f[1]};
+        for (int k = 0; k < 3; ++k)
+            F[k] = df_add(two_sum(ls.s[k], ls.e[k]), df_mul_f(r18, (float)ls.n[k]));
+    }
+}
+
+// Lever arm r_F = x_F - x_C of fluid cell (x, y, z) from body p's centre,
+// minimum image on periodic axes: FP64 on FP64 lattices, else a double-float
+// from the body's FP32 record.
+template <int PREC>
+__device__ __forceinline__ void lever_arm(const SweepArgs &a, const LatDev &L, uint32_t p, int x, int y, int z,
+                                          typename Acc<PREC>::V r[3]) {
+    const int xs[3] = {x, y, z}, ns[3] = {L.nx, L.ny, L.nz}, per[3] = {L.px, L.py, L.pz};
+    if constexpr (PREC == LBM_F64) {
+        for (int k = 0; k < 3; ++k) r[k] = min_image((double)xs[k] - a.P.pos[3 * (size_t)p + k], ns[k], per[k]);
+    } else {
+        const float *bf = a.P.bodyf + BF_STRIDE * (size_t)p;
+        for (int k = 0; k < 3; ++k) {
+            df d = two_sum((float)xs[k], -bf[BF_POS + k]);
+            d = df_add_f(d, -bf[BF_POSLO + k]);
+            if (per[k]) {
+                if (d.hi > 0.5f * (float)ns[k])
+                    d = df_add_f(d, -(float)ns[k]);
+                else if (d.hi < -0.5f * (float)ns[k])
+                    d = df_add_f(d, (float)ns[k]);
+            }
+            r[k] = d;
+        }
+    }
+}
+
+// Hand a body's per-cell momentum F and torque r_F x F to the partial sums
+// (the torque of link q is (r_F + c_q) x dF_q = r_F x dF_q since dF_q || c_q).
+template <int PREC>
+__device__ __forceinline__ void body_add(const SweepArgs &a, uint32_t *tkey, typename Acc<PREC>::V *tval,
+                                         uint32_t key, const typename Acc<PREC>::V F[3],
+                                         const typename Acc<PREC>::V r[3]) {
+    using A = Acc<PREC>;
+    typename A::V v[6] = {F[0], F[1], F[2],
+                          A::sub(A::mul(r[1], F[2]), A::mul(r[2], F[1])),
+                          A::sub(A::mul(r[2], F[0]), A::mul(r[0], F[2])),
+                          A::sub(A::mul(r[0], F[1]), A::mul(r[1], F[0]))};
+    tacc_add<PREC>(a, tkey, tval, key, v, 6);
 }
 
 // Velocity bounce-back of one link (Eq. LBMMovWall) and its momentum
-// exchange (Eqs. TransferredMomentum, LBMhydrodynForce).  ft is the
+// exchange (Eqs. TransferredMomentum, LBMhydrodynForce), generic over the
+// neighbour (either wall layer or any body), in FP64.  ft is the
 // post-collision offset f~_q - w_q rho0 of the fluid cell; returns the offset
 // of the reflected population f~_q - 6 w_q rho0 c_q.u_s.  The momentum
 // (2 f~_q - 6 w_q rho0 c_q.u_s) c_q, and its torque (x_s - x_C) x dF about the
-// body centre, go into this thread's partial-sum entry.
+// body centre, go into this thread's partial-sum entry.  Used for links to a
+// second body of the same cell (the first body's links are handled inline).
+template <int PREC>
 __device__ __noinline__ double bounce_link(const SweepArgs &a, const LatDev &L, int li, int q, int nb,
                                            int xs, int ys, int zs, double ft, uint32_t *tkey,
-                                           double *tval, Slots *sh) {
+                                           typename Acc<PREC>::V *tval) {
+    using A = Acc<PREC>;
     const uint32_t id = a.pid[L.c_off + nb];
     double us[3] = {0.0, 0.0, 0.0}, r[3] = {0.0, 0.0, 0.0};
     uint32_t key = SLOT_EMPTY;
@@ -231,7 +318,9 @@ __device__ __noinline__ double bounce_link(const SweepArgs &a, const LatDev &L, 
         v[3] = r[1] * v[2] - r[2] * v[1];
         v[4] = r[2] * v[0] - r[0] * v[2];
         v[5] = r[0] * v[1] - r[1] * v[0];
-        tacc_add(a, tkey, tval, key, v, 6);
+        typename A::V va[6];
+        for (int k = 0; k < 6; ++k) va[k] = A::from(v[k]);
+        tacc_add<PREC>(a, tkey, tval, key, va, 6);
     }
     return ft - dbb;
 }
@@ -291,7 +380,7 @@ __device__ __forceinline__ typename Store<PREC>::C ring_value(const typename Rin
 // never need an address (which would put them in local memory on every path).
 template <int PREC, int ODD, int VIEW>
 __device__ __noinline__ void near_cell(const SweepArgs &a, const LatDev &L, int li, int idx,
-                                       uint32_t *tkey, double *tval, Slots *sh, const void *src) {
+                                       uint32_t *tkey, typename Acc<PREC>::V *tval, const void *src) {
     using S = Store<PREC>;
     using T = typename S::T;
     using C = typename S::C;
@@ -331,9 +420,9 @@ __device__ __noinline__ void near_cell(const SweepArgs &a, const LatDev &L, int 
         }
     }
     // Obstacle links: the ids of all obstacle neighbours are requested in one
-    // round trip; the first body met (p0) has its state loaded once and its
-    // links are bounced inline, in FP64, with the force and torque summed in
-    // registers; links to any further body take bounce_link.
+    // round trip; the first body met (p0) has its motion loaded once and its
+    // links are bounced inline in the compute precision, their momentum
+    // gathered in a LinkSum; links to any further body take bounce_link.
     const uint32_t obst = solid & ~wall;
     uint32_t p0 = SLOT_EMPTY, m0 = 0;
     if (obst) {
@@ -348,24 +437,29 @@ __device__ __noinline__ void near_cell(const SweepArgs &a, const LatDev &L, int 
                 if (ids[q] == p0) m0 |= 1u << q;
             }
     }
-    double bpos[3] = {0, 0, 0}, bU[3] = {0, 0, 0}, bW[3] = {0, 0, 0};
+    // body p0: lever arm r_F of this cell, velocity U and angular velocity W
+    using A = Acc<PREC>;
+    typename A::V rF[3];
+    C rc[3] = {0, 0, 0}, bU[3] = {0, 0, 0}, bW[3] = {0, 0, 0};
     if (p0 != SLOT_EMPTY) {
+        lever_arm<PREC>(a, L, p0, cg.x, cg.y, cg.z, rF);
         for (int k = 0; k < 3; ++k) {
-            bpos[k] = a.P.pos[3 * (size_t)p0 + k];
-            bU[k] = a.P.vel[3 * (size_t)p0 + k];
-            bW[k] = a.P.om[3 * (size_t)p0 + k];
+            if constexpr (PREC == LBM_F64) {
+                rc[k] = rF[k];
+                bU[k] = a.P.vel[3 * (size_t)p0 + k];
+                bW[k] = a.P.om[3 * (size_t)p0 + k];
+            } else {
+                rc[k] = rF[k].hi;
+                bU[k] = a.P.bodyf[BF_STRIDE * (size_t)p0 + BF_U + k];
+                bW[k] = a.P.bodyf[BF_STRIDE * (size_t)p0 + BF_W + k];
+            }
         }
     }
-    double bacc[6] = {0, 0, 0, 0, 0, 0};
-    collide<C>(g, C(L.omega), C(L.omega_odd), C(L.rho0), C(L.g[0]), C(L.g[1]), C(L.g[2]));
-    // Wall links are bounced inline in the compute precision: the wall layer
-    // that is hit follows from the neighbour's y (a y = 0 or y = ny-1 layer
-    // of a non-periodic y axis moves, any other wall layer rests).  Their
-    // momentum is summed per cell as a small part (2 f~ - 6 w rho0 c.u_w, with
-    // f~ the stored offset) and the constant part 2 w rho0 c, then handed to
-    // the FP64 per-thread partial once.  Obstacle (particle) links go through
-    // bounce_link in FP64.
-    C wsmall[3] = {0, 0, 0}, wconst[3] = {0, 0, 0};
+    collide<C>(g, C(L.omega), C(L.omega_odd), C(L.rho0), C(L.inv_rho0), C(L.g[0]), C(L.g[1]), C(L.g[2]));
+    // Wall links are bounced inline as well: the wall layer that is hit
+    // follows from the neighbour's y (a y = 0 or y = ny-1 layer of a
+    // non-periodic y axis moves, any other wall layer rests).
+    LinkSum<C> lw, lb;
     int wside = -1;
     const C rho0c = C(L.rho0);
 #pragma unroll
@@ -386,47 +480,35 @@ __device__ __noinline__ void near_cell(const SweepArgs &a, const LatDev &L, int 
             if (cy(q)) cu += cy(q) > 0 ? u1 : -u1;
             if (cz(q)) cu += cz(q) > 0 ? u2 : -u2;
             const C dbb = C(6.0 * wq(q)) * rho0c * cu;
-            const C val = g[q] - dbb;
             if (side >= 0) {
-                if (wside >= 0 && side != wside) {  // a cell touching both y walls (ny = 3): flush first
-                    double v[6] = {(double)wsmall[0] + (double)wconst[0], (double)wsmall[1] + (double)wconst[1],
-                                   (double)wsmall[2] + (double)wconst[2], 0, 0, 0};
-                    double *gacc = global_acc(a, KEY_WALL | ((uint32_t)li << 1) | (uint32_t)wside);
-                    for (int k = 0; k < 3; ++k) atomicAdd(gacc + k, v[k]);
-                    wsmall[0] = wsmall[1] = wsmall[2] = wconst[0] = wconst[1] = wconst[2] = 0;
+                if (wside >= 0 && side != wside) {  // a cell touching both y walls (ny = 3): hand over first
+                    typename A::V F[3];
+                    link_force<PREC>(L, lw, F);
+                    tacc_add<PREC>(a, tkey, tval, KEY_WALL | ((uint32_t)li << 1) | (uint32_t)wside, F, 3);
+                    lw = LinkSum<C>();
                 }
                 wside = side;
-                const C ms = C(2) * g[q] - dbb, mc = C(2.0 * wq(q)) * rho0c;
-                if (cx(q)) { wsmall[0] += cx(q) > 0 ? ms : -ms; wconst[0] += cx(q) > 0 ? mc : -mc; }
-                if (cy(q)) { wsmall[1] += cy(q) > 0 ? ms : -ms; wconst[1] += cy(q) > 0 ? mc : -mc; }
-                if (cz(q)) { wsmall[2] += cz(q) > 0 ? ms : -ms; wconst[2] += cz(q) > 0 ? mc : -mc; }
+                lw.link(q, C(2) * g[q] - dbb);
             }
-            S::st(base + opp(q) * np + idx, val);
+            S::st(base + opp(q) * np + idx, g[q] - dbb);
         } else if ((m0 >> q) & 1u) {
-            // velocity bounce-back off body p0 (Eq. LBMMovWall) and the link's
-            // momentum (2 f~ - 6 w rho0 c.u_s) c and torque (x_s - x_C) x dF
-            const double r0 = min_image((double)wrapc(cg.x + cx(q), L.nx) - bpos[0], L.nx, L.px);
-            const double r1 = min_image((double)wrapc(cg.y + cy(q), L.ny) - bpos[1], L.ny, L.py);
-            const double r2 = min_image((double)wrapc(cg.z + cz(q), L.nz) - bpos[2], L.nz, L.pz);
-            const double us0 = bU[0] + (bW[1] * r2 - bW[2] * r1);
-            const double us1 = bU[1] + (bW[2] * r0 - bW[0] * r2);
-            const double us2 = bU[2] + (bW[0] * r1 - bW[1] * r0);
-            const double cu = cx(q) * us0 + cy(q) * us1 + cz(q) * us2;
-            const double dbb = 6.0 * wq(q) * L.rho0 * cu;
-            const double ft = (double)g[q];
-            S::st(base + opp(q) * np + idx, (C)(ft - dbb));
-            const double mag = 2.0 * (ft + wq(q) * L.rho0) - dbb;
-            const double f0 = mag * cx(q), f1 = mag * cy(q), f2 = mag * cz(q);
-            bacc[0] += f0;
-            bacc[1] += f1;
-            bacc[2] += f2;
-            bacc[3] += r1 * f2 - r2 * f1;
-            bacc[4] += r2 * f0 - r0 * f2;
-            bacc[5] += r0 * f1 - r1 * f0;
+            // velocity bounce-back off body p0 (Eq. LBMMovWall): u_s at the
+            // obstacle cell x_F + c_q, lever arm r_F + c_q
+            const C r0 = rc[0] + C(cx(q)), r1 = rc[1] + C(cy(q)), r2 = rc[2] + C(cz(q));
+            const C us0 = bU[0] + (bW[1] * r2 - bW[2] * r1);
+            const C us1 = bU[1] + (bW[2] * r0 - bW[0] * r2);
+            const C us2 = bU[2] + (bW[0] * r1 - bW[1] * r0);
+            C cu = 0;
+            if (cx(q)) cu += cx(q) > 0 ? us0 : -us0;
+            if (cy(q)) cu += cy(q) > 0 ? us1 : -us1;
+            if (cz(q)) cu += cz(q) > 0 ? us2 : -us2;
+            const C dbb = C(6.0 * wq(q)) * rho0c * cu;
+            S::st(base + opp(q) * np + idx, g[q] - dbb);
+            lb.link(q, C(2) * g[q] - dbb);
         } else if ((solid >> q) & 1u) {
-            const double v = bounce_link(a, L, li, q, idx + nb_off(cg, q), wrapc(cg.x + cx(q), L.nx),
-                                         wrapc(cg.y + cy(q), L.ny), wrapc(cg.z + cz(q), L.nz),
-                                         (double)g[q], tkey, tval, sh);
+            const double v = bounce_link<PREC>(a, L, li, q, idx + nb_off(cg, q), wrapc(cg.x + cx(q), L.nx),
+                                               wrapc(cg.y + cy(q), L.ny), wrapc(cg.z + cz(q), L.nz),
+                                               (double)g[q], tkey, tval);
             S::st(base + opp(q) * np + idx, (C)v);
         } else if (!ODD) {
             S::st(base + opp(q) * np + idx, g[q]);
@@ -434,23 +516,27 @@ __device__ __noinline__ void near_cell(const SweepArgs &a, const LatDev &L, int 
             S::st(base + q * np + idx + nb_off(cg, q), g[q]);
         }
     }
-    if (p0 != SLOT_EMPTY) tacc_add(a, tkey, tval, p0, bacc, 6);
+    if (p0 != SLOT_EMPTY) {
+        typename A::V F[3];
+        link_force<PREC>(L, lb, F);
+        body_add<PREC>(a, tkey, tval, p0, F, rF);
+    }
     if (wside >= 0) {
-        const uint32_t key = KEY_WALL | ((uint32_t)li << 1) | (uint32_t)wside;
-        double v[3];
-        for (int k = 0; k < 3; ++k) v[k] = (double)wsmall[k] + (double)wconst[k];
-        tacc_add(a, tkey, tval, key, v, 3);
+        typename A::V F[3];
+        link_force<PREC>(L, lw, F);
+        tacc_add<PREC>(a, tkey, tval, KEY_WALL | ((uint32_t)li << 1) | (uint32_t)wside, F, 3);
     }
 }
 
 // Fluid cell whose only wall/obstacle neighbours are the moving wall layer
 // y = 0 (SIDE 0) or y = ny-1 (SIDE 1): the bounced directions are the five with
-// c_y = -1 (resp. +1), known at compile time, so the whole update stays in the
-// bulk path's registers.  On odd steps the five populations arriving from the
-// layer are the ones the previous step bounced into slot q of x itself.
+// c_y = -1 (resp. +1), known at compile time.  On odd steps the five
+// populations arriving from the layer are the ones the previous step bounced
+// into slot q of x itself.  Out of line, with its own loads, so that the
+// caller's bulk path keeps its registers.
 template <int PREC, int ODD, int SIDE>
 __device__ __noinline__ void wall_cell(const SweepArgs &a, const LatDev &L, int li, int idx,
-                                          uint32_t *tkey, double *tval) {
+                                       uint32_t *tkey, typename Acc<PREC>::V *tval) {
     using S = Store<PREC>;
     using T = typename S::T;
     using C = typename S::C;
@@ -468,10 +554,10 @@ __device__ __noinline__ void wall_cell(const SweepArgs &a, const LatDev &L, int 
 #pragma unroll
         for (int q = 0; q < Q; ++q) g[q] = S::ld(base + q * np + idx);
     }
-    collide<C>(g, C(L.omega), C(L.omega_odd), C(L.rho0), C(L.g[0]), C(L.g[1]), C(L.g[2]));
+    collide<C>(g, C(L.omega), C(L.omega_odd), C(L.rho0), C(L.inv_rho0), C(L.g[0]), C(L.g[1]), C(L.g[2]));
     const double *uw = SIDE == 0 ? L.wlo : L.whi;
     const C u0 = C(uw[0]), u1 = C(uw[1]), u2 = C(uw[2]), rho0c = C(L.rho0);
-    C ws[3] = {0, 0, 0}, wc[3] = {0, 0, 0};
+    LinkSum<C> lw;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         if (SIDE == 0 ? cy(q) < 0 : cy(q) > 0) {
@@ -481,20 +567,16 @@ __device__ __noinline__ void wall_cell(const SweepArgs &a, const LatDev &L, int 
             if (cz(q)) cu += cz(q) > 0 ? u2 : -u2;
             const C dbb = C(6.0 * wq(q)) * rho0c * cu;
             S::st(base + opp(q) * np + idx, g[q] - dbb);
-            const C ms = C(2) * g[q] - dbb, mc = C(2.0 * wq(q)) * rho0c;
-            if (cx(q)) { ws[0] += cx(q) > 0 ? ms : -ms; wc[0] += cx(q) > 0 ? mc : -mc; }
-            ws[1] += cy(q) > 0 ? ms : -ms;
-            wc[1] += cy(q) > 0 ? mc : -mc;
-            if (cz(q)) { ws[2] += cz(q) > 0 ? ms : -ms; wc[2] += cz(q) > 0 ? mc : -mc; }
+            lw.link(q, C(2) * g[q] - dbb);
         } else if (!ODD) {
             S::st(base + opp(q) * np + idx, g[q]);
         } else {
             S::st(base + q * np + idx + nb_off(cg, q), g[q]);
         }
     }
-    double v[3];
-    for (int k = 0; k < 3; ++k) v[k] = (double)ws[k] + (double)wc[k];
-    tacc_add(a, tkey, tval, KEY_WALL | ((uint32_t)li << 1) | (uint32_t)SIDE, v, 3);
+    typename Acc<PREC>::V F[3];
+    link_force<PREC>(L, lw, F);
+    tacc_add<PREC>(a, tkey, tval, KEY_WALL | ((uint32_t)li << 1) | (uint32_t)SIDE, F, 3);
 }
 
 // Fluid cell with fluid neighbours only.
@@ -513,7 +595,7 @@ __device__ __forceinline__ void bulk_cell(const SweepArgs &a, const LatDev &L, i
         else
             g[q] = S::ld(base + opp(q) * np + idx + nb_off(cg, opp(q)));
     }
-    collide<C>(g, C(L.omega), C(L.omega_odd), C(L.rho0), C(L.g[0]), C(L.g[1]), C(L.g[2]));
+    collide<C>(g, C(L.omega), C(L.omega_odd), C(L.rho0), C(L.inv_rho0), C(L.g[0]), C(L.g[1]), C(L.g[2]));
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         if (!ODD)
@@ -529,43 +611,49 @@ __device__ __forceinline__ void bulk_cell(const SweepArgs &a, const LatDev &L, i
 template <int PREC> struct SweepBounds { static constexpr int MINB = 3; };
 template <> struct SweepBounds<LBM_F64> { static constexpr int MINB = 2; };
 
-// SINGLE: one lattice, whose parameters travel in the kernel's parameter
-// space (a.lat0) and are read as constant-bank operands; otherwise each tile
-// finds its lattice in the global table by binary search on tile0.
-// Hand the per-thread partial sums to the global accumulators, warp by warp:
-// lanes holding the same key (body or wall) are summed by the lowest of them,
-// which issues one FP64 atomic per component.  No block barrier, so blocks
-// without wall or obstacle links never wait on each other's warps.
-__device__ __forceinline__ void flush_forces(const SweepArgs &a, Slots &, uint32_t *tkey,
-                                             double (*tval)[6]) {
+// Hand the per-thread partial sums to the global accumulators, warp by warp
+// and key by key (body or wall): the lanes holding the key add their partials
+// in a butterfly over the warp (the others add zero), and the lowest of them
+// issues one FP64 atomic per component.  No block barrier, so blocks without
+// wall or obstacle links never wait on each other's warps; warps without any
+// key leave after one vote.
+template <int PREC>
+__device__ __forceinline__ void flush_forces(const SweepArgs &a, uint32_t *tkey,
+                                             typename Acc<PREC>::V (*tval)[6]) {
+    using A = Acc<PREC>;
     __syncwarp();
-    const uint32_t key = tkey[threadIdx.x];
-    const uint32_t grp = __match_any_sync(0xffffffffu, key);
     const int lane = threadIdx.x & 31;
-    if (key != SLOT_EMPTY && lane == __ffs(grp) - 1) {
-        double v[6] = {0, 0, 0, 0, 0, 0};
-        const int wbase = threadIdx.x - lane;
-        for (uint32_t m = grp; m; m &= m - 1) {
-            const int l = __ffs(m) - 1;
-            for (int k = 0; k < 6; ++k) v[k] += tval[wbase + l][k];
+    uint32_t key = tkey[threadIdx.x];
+    for (uint32_t pending = __ballot_sync(0xffffffffu, key != SLOT_EMPTY); pending;
+         pending = __ballot_sync(0xffffffffu, key != SLOT_EMPTY)) {
+        const int leader = __ffs(pending) - 1;
+        const uint32_t k0 = __shfl_sync(0xffffffffu, key, leader);
+        const bool mine = key == k0;
+        const int nv = (k0 & KEY_WALL) ? 3 : 6;
+        double *g = global_acc(a, k0);
+        for (int k = 0; k < nv; ++k) {
+            typename A::V v = mine ? tval[threadIdx.x][k] : A::zero();
+#pragma unroll
+            for (int o = 16; o; o >>= 1) v = A::add(v, A::shfl_xor(v, o));
+            if (lane == leader) atomicAdd(g + k, A::to_double(v));
         }
-        double *g = global_acc(a, key);
-        const int nv = (key & KEY_WALL) ? 3 : 6;
-        for (int k = 0; k < nv; ++k) atomicAdd(g + k, v[k]);
+        if (mine) key = SLOT_EMPTY;
     }
 }
 
 // Direct sweep, one cell per thread: plain stream-collide for bulk cells,
 // the wall and near-obstacle paths for cells flagged F_YLO/F_YHI or F_NEAR.
+// SINGLE: one lattice, whose parameters travel in the kernel's parameter
+// space (a.lat0) and are read as constant-bank operands; otherwise each tile
+// finds its lattice in the global table by binary search on tile0.
 template <int PREC, int ODD, bool SINGLE>
 __global__ void __launch_bounds__(256, SweepBounds<PREC>::MINB)
     sweep_kernel(const __grid_constant__ SweepArgs a) {
     using S = Store<PREC>;
     using T = typename S::T;
     using C = typename S::C;
-    __shared__ Slots sh;
     __shared__ uint32_t tkey[256];
-    __shared__ double tval[256][6];
+    __shared__ typename Acc<PREC>::V tval[256][6];
     tkey[threadIdx.x] = SLOT_EMPTY;
 
     for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
@@ -597,10 +685,10 @@ __global__ void __launch_bounds__(256, SweepBounds<PREC>::MINB)
             continue;
         }
         if (fl & F_NEAR) {  // reload from global memory inside the near path
-            near_cell<PREC, ODD, 0>(a, L, li, idx, &tkey[threadIdx.x], tval[threadIdx.x], &sh, nullptr);
+            near_cell<PREC, ODD, 0>(a, L, li, idx, &tkey[threadIdx.x], tval[threadIdx.x], nullptr);
             continue;
         }
-        collide<C>(g, C(L.omega), C(L.omega_odd), C(L.rho0), C(L.g[0]), C(L.g[1]), C(L.g[2]));
+        collide<C>(g, C(L.omega), C(L.omega_odd), C(L.rho0), C(L.inv_rho0), C(L.g[0]), C(L.g[1]), C(L.g[2]));
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
             if (!ODD)
@@ -609,7 +697,7 @@ __global__ void __launch_bounds__(256, SweepBounds<PREC>::MINB)
                 S::st(base + q * np + idx + nb_off(cg, q), g[q]);
         }
     }
-    flush_forces(a, sh, tkey, tval);
+    flush_forces<PREC>(a, tkey, tval);
 }
 
 // ---------------------------------------------------------------------------
@@ -710,7 +798,7 @@ __device__ __forceinline__ void bulk_cell_staged(const SweepArgs &a, const LatDe
 #pragma unroll
     for (int q = 0; q < Q; ++q)
         g[q] = S::ld(stage + q * Cfg::W + (ODD ? (L.off[opp(q)] & (Cfg::A - 1)) : 0) + threadIdx.x);
-    collide<C>(g, C(L.omega), C(L.omega_odd), C(L.rho0), C(L.g[0]), C(L.g[1]), C(L.g[2]));
+    collide<C>(g, C(L.omega), C(L.omega_odd), C(L.rho0), C(L.inv_rho0), C(L.g[0]), C(L.g[1]), C(L.g[2]));
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         if (!ODD)
@@ -729,13 +817,12 @@ __global__ void __launch_bounds__(256, SweepBounds<PREC>::MINB)
     extern __shared__ __align__(128) unsigned char dsm[];
     T *stages = reinterpret_cast<T *>(dsm);
     __shared__ __align__(8) uint64_t bars[Cfg::S];
-    __shared__ Slots sh;
     __shared__ uint32_t tkey[256];
-    __shared__ double tval[256][6];
+    __shared__ typename Acc<PREC>::V tval[256][6];
     const int tid = threadIdx.x;
     tkey[tid] = SLOT_EMPTY;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) tval[tid][k] = 0.0;
+    for (int k = 0; k < 6; ++k) tval[tid][k] = Acc<PREC>::zero();
     if (tid == 0) {
         for (int s = 0; s < Cfg::S; ++s) mbar_init(&bars[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -796,9 +883,9 @@ __global__ void __launch_bounds__(256, SweepBounds<PREC>::MINB)
                         cg.dzp = cg.z == L.nz - 1 ? -(L.nz - 1) * sz : sz;
                         if (fl & F_NEAR) {
                             if (interior)
-                                near_cell<PREC, ODD, 1>(a, L, li, idx, &tkey[tid], tval[tid], &sh, stage);
+                                near_cell<PREC, ODD, 1>(a, L, li, idx, &tkey[tid], tval[tid], stage);
                             else
-                                near_cell<PREC, ODD, 0>(a, L, li, idx, &tkey[tid], tval[tid], &sh, nullptr);
+                                near_cell<PREC, ODD, 0>(a, L, li, idx, &tkey[tid], tval[tid], nullptr);
                         } else {
                             bulk_cell<PREC, ODD>(a, L, idx, cg);
                         }
@@ -822,7 +909,7 @@ __global__ void __launch_bounds__(256, SweepBounds<PREC>::MINB)
         }
         __syncthreads();
     }
-    flush_forces(a, sh, tkey, tval);
+    flush_forces<PREC>(a, tkey, tval);
 }
 
 // ---------------------------------------------------------------------------
@@ -884,13 +971,12 @@ __global__ void __launch_bounds__(256, SweepBounds<PREC>::MINB)
     using Word = typename Cfg::Word;
     extern __shared__ __align__(128) unsigned char dsm[];
     Word *ring = reinterpret_cast<Word *>(dsm);
-    __shared__ Slots sh;
     __shared__ uint32_t tkey[256];
-    __shared__ double tval[256][6];
+    __shared__ typename Acc<PREC>::V tval[256][6];
     const int tid = threadIdx.x;
     tkey[tid] = SLOT_EMPTY;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) tval[tid][k] = 0.0;
+    for (int k = 0; k < 6; ++k) tval[tid][k] = Acc<PREC>::zero();
 
     const int nk = blockIdx.x < (unsigned)a.ntiles ? (a.ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     // prologue: tiles 0 .. D-1 (one commit group per tile, empty groups included)
@@ -927,14 +1013,14 @@ __global__ void __launch_bounds__(256, SweepBounds<PREC>::MINB)
         if (fl & F_SOLID) continue;
         const CellGeom cg = cell_geom(L, idx);
         if (fl & F_NEAR) {
-            near_cell<PREC, ODD, 2>(a, L, li, idx, &tkey[tid], tval[tid], &sh, col);
+            near_cell<PREC, ODD, 2>(a, L, li, idx, &tkey[tid], tval[tid], col);
             continue;
         }
         C g[Q];
 #pragma unroll
         for (int q = 0; q < Q; ++q)
             g[q] = ring_value<PREC>(col, q, ODD ? ((idx + nb_off(cg, opp(q))) & 1) : (idx & 1));
-        collide<C>(g, C(L.omega), C(L.omega_odd), C(L.rho0), C(L.g[0]), C(L.g[1]), C(L.g[2]));
+        collide<C>(g, C(L.omega), C(L.omega_odd), C(L.rho0), C(L.inv_rho0), C(L.g[0]), C(L.g[1]), C(L.g[2]));
         T *base = reinterpret_cast<T *>(a.f) + L.f_off;
         const long long np = L.npad;
 #pragma unroll
@@ -946,7 +1032,7 @@ __global__ void __launch_bounds__(256, SweepBounds<PREC>::MINB)
         }
     }
     cp_async_wait<0>();
-    flush_forces(a, sh, tkey, tval);
+    flush_forces<PREC>(a, tkey, tval);
 }
 
 // variant: SWEEP_DIRECT (one cell per thread, `block` threads), SWEEP_STAGED
