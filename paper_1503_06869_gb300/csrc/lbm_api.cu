@@ -37,6 +37,7 @@ struct lbm_ctx {
     uint8_t *flags = nullptr;
     uint32_t *pid = nullptr, *pid_prev = nullptr;
     double *wall_acc = nullptr, *wall_last = nullptr;
+    uint32_t *tbits = nullptr;      // direct sweep: tiles that may hold non-bulk cells
     uint32_t *err = nullptr;
 
     int np = 0;
@@ -172,6 +173,7 @@ SweepArgs sweep_args(lbm_ctx *ctx) {
     a.P = ctx->P;
     a.wall_acc = ctx->wall_acc;
     a.err = ctx->err;
+    a.tbits = ctx->variant == SWEEP_DIRECT ? ctx->tbits : nullptr;
     return a;
 }
 
@@ -187,7 +189,17 @@ RemapArgs remap_args(lbm_ctx *ctx) {
     a.wall_last = ctx->wall_last;
     a.nlat = ctx->nlat;
     a.err = ctx->err;
+    a.tbits = ctx->variant == SWEEP_DIRECT ? ctx->tbits : nullptr;
+    a.tile = tile_cells(ctx);
     return a;
+}
+
+// Recount the direct sweep's tile bits from the flags (clears stale marks).
+lbm_status recount_tiles(lbm_ctx *ctx) {
+    if (ctx->variant != SWEEP_DIRECT) return LBM_OK;
+    CK(launch_tile_bits(remap_args(ctx), ctx->ntiles, ctx->stream));
+    ctx->launches += 1;
+    return LBM_OK;
 }
 
 lbm_status upload_lattices(lbm_ctx *ctx) {
@@ -405,8 +417,13 @@ lbm_status create_common(const lbm_grid_desc *cells, int ncells, lbm_ctx **out) 
     ctx->wall_acc = (double *)owned_alloc(ctx, sizeof(double) * 6 * ACC_COPIES * ncells);
     ctx->wall_last = (double *)owned_alloc(ctx, sizeof(double) * 6 * ncells);
     ctx->err = (uint32_t *)owned_alloc(ctx, 16);
+    {
+        long long tiles32 = 0;  // tiles of the smallest direct-sweep tile (32 cells)
+        for (auto &L : ctx->lat_h) tiles32 += (L.n + 31) / 32;
+        ctx->tbits = (uint32_t *)owned_alloc(ctx, sizeof(uint32_t) * (size_t)(tiles32 / 32 + 1));
+    }
     if (!ctx->lat_d || !ctx->f || !ctx->flags || !ctx->pid || !ctx->pid_prev || !ctx->wall_acc ||
-        !ctx->wall_last || !ctx->err) {
+        !ctx->wall_last || !ctx->err || !ctx->tbits) {
         lbm_destroy(ctx);
         return LBM_ERR_OOM;
     }
@@ -435,7 +452,7 @@ lbm_status create_common(const lbm_grid_desc *cells, int ncells, lbm_ctx **out) 
         ctx->launches += 2;
     }
     ctx->grid = default_grid(ctx);
-    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+    if (recount_tiles(ctx) != LBM_OK || cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
         lbm_destroy(ctx);
         return LBM_ERR_CUDA;
     }
@@ -484,7 +501,7 @@ lbm_status lbm_set_particles(lbm_ctx *ctx, const lbm_particle *p, int n) {
     if (n < 0 || (n > 0 && !p)) return fail(ctx, LBM_ERR_ARG, "bad particle array");
     // validate and derive host-side quantities
     std::vector<double> pos(3 * n), quat(4 * n), vel(3 * n), om(3 * n), L(3 * n), semi(3 * n), mass(n),
-        inertia(3 * n), extF(3 * n), extM(3 * n), minv(n), Iinv(3 * n);
+        inertia(3 * n), extF(3 * n), extM(3 * n), minv(n), Iinv(3 * n), R64(9 * (size_t)n);
     std::vector<float> bodyf(BF_STRIDE * (size_t)n, 0.0f);
     std::vector<int> cell(n), fixed(n), region(6 * n);
     for (int i = 0; i < n; ++i) {
@@ -543,6 +560,7 @@ lbm_status lbm_set_particles(lbm_ctx *ctx, const lbm_particle *p, int n) {
         mass[i] = m;
         minv[i] = 1.0 / m;
         for (int a = 0; a < 3; ++a) Iinv[3 * i + a] = 1.0 / I[a];
+        for (int k = 0; k < 9; ++k) R64[9 * (size_t)i + k] = R[k];
         float *bf = &bodyf[BF_STRIDE * (size_t)i];
         for (int k = 0; k < 9; ++k) bf[BF_R + k] = (float)R[k];
         for (int a = 0; a < 3; ++a) {
@@ -589,6 +607,7 @@ lbm_status lbm_set_particles(lbm_ctx *ctx, const lbm_particle *p, int n) {
     P.minv = part_alloc<double>(ctx, m);
     P.Iinv = part_alloc<double>(ctx, 3 * m);
     P.bodyf = part_alloc<float>(ctx, BF_STRIDE * m);
+    P.R64 = part_alloc<double>(ctx, 9 * m);
     P.extF = part_alloc<double>(ctx, 3 * m);
     P.extM = part_alloc<double>(ctx, 3 * m);
     P.cell = part_alloc<int>(ctx, m);
@@ -621,6 +640,7 @@ lbm_status lbm_set_particles(lbm_ctx *ctx, const lbm_particle *p, int n) {
     CK(up(P.minv, minv.data(), 8 * minv.size()));
     CK(up(P.Iinv, Iinv.data(), 8 * Iinv.size()));
     CK(up(P.bodyf, bodyf.data(), 4 * bodyf.size()));
+    CK(up(P.R64, R64.data(), 8 * R64.size()));
     CK(up(P.extF, extF.data(), 8 * extF.size()));
     CK(up(P.extM, extM.data(), 8 * extM.size()));
     CK(up(P.cell, cell.data(), 4 * cell.size()));
@@ -640,6 +660,8 @@ lbm_status lbm_set_particles(lbm_ctx *ctx, const lbm_particle *p, int n) {
     for (int li = 0; li < ctx->nlat; ++li)
         CK(launch_remap_full(ctx->prec, next_odd, ra, ctx->lat_h[li], li, ctx->stream));
     ctx->launches += 3 * ctx->nlat + (n > 0 ? 1 : 0);
+    lbm_status st = recount_tiles(ctx);
+    if (st != LBM_OK) return st;
     CK(cudaStreamSynchronize(ctx->stream));
     return LBM_OK;
 }
@@ -649,10 +671,17 @@ lbm_status lbm_step(lbm_ctx *ctx, int nsteps) {
     if (nsteps < 0) return fail(ctx, LBM_ERR_ARG, "nsteps < 0");
     if (ctx->broken) return fail(ctx, LBM_ERR_STATE, "context stopped after an earlier error");
     int left = nsteps;
+    // the direct sweep's tile bits are recounted every 64 steps (moving
+    // bodies leave marked tiles behind; a stale mark only costs time)
+    const bool moving = ctx->np > 0 && ctx->variant == SWEEP_DIRECT;
+    auto maybe_recount = [&]() -> lbm_status {
+        return (moving && (ctx->t & 63) == 0) ? recount_tiles(ctx) : LBM_OK;
+    };
     const bool use_graph = ctx->graphs && !ctx->timing && ctx->stream != nullptr;
     if (use_graph && left >= 2) {
         if (ctx->t & 1) {
             lbm_status s = enqueue_step(ctx, false);
+            if (s == LBM_OK) s = maybe_recount();
             if (s != LBM_OK) return s;
             --left;
         }
@@ -667,11 +696,14 @@ lbm_status lbm_step(lbm_ctx *ctx, int nsteps) {
                 ctx->t += 2;
                 ctx->launches += per;
                 left -= 2;
+                lbm_status s = maybe_recount();
+                if (s != LBM_OK) return s;
             }
         }
     }
     while (left > 0) {
         lbm_status s = enqueue_step(ctx, ctx->timing);
+        if (s == LBM_OK) s = maybe_recount();
         if (s != LBM_OK) return s;
         --left;
     }
@@ -922,6 +954,8 @@ lbm_status lbm_set_launch(lbm_ctx *ctx, int block, int grid) {
     if (s != LBM_OK) return s;
     ctx->grid = grid > 0 ? (grid < ctx->ntiles ? grid : ctx->ntiles) : default_grid(ctx);
     drop_graph(ctx);
+    s = recount_tiles(ctx);  // the tile size may have changed
+    if (s != LBM_OK) return s;
     CK(cudaStreamSynchronize(ctx->stream));
     return LBM_OK;
 }

@@ -9,6 +9,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "../../include/lbm.h"
 
 namespace lbm {
@@ -93,6 +95,7 @@ struct PartDev {
     double *semi, *mass, *inertia;       // shape: semi-axes, mass, body inertia diag
     double *minv, *Iinv;                 // 1/mass, 1/inertia (host-computed)
     float *bodyf;                        // BF_STRIDE per body, layout BF_* below
+    double *R64;                         // 9 per body: rotation of quat, rounded as the mapping's inside test
     double *extF, *extM;                 // external loads
     int *cell, *fixed;
     double *pos_old, *vel_old, *om_old, *quat_old; // state before this step's update
@@ -118,6 +121,10 @@ struct SweepArgs {
     PartDev P;
     double *wall_acc;        // 6 per lattice: y-low wall F, y-high wall F
     uint32_t *err;           // device error word
+    // direct sweep: bit t of tbits set = tile t may hold a cell with a nonzero
+    // flag; a clear bit guarantees that every cell of the tile is bulk fluid
+    // (null: every tile is treated as flagged)
+    const uint32_t *tbits;
 };
 
 // Storage forms: every form holds g_q = f_q - w_q rho0 (the offset from rest).
@@ -197,6 +204,37 @@ __device__ __forceinline__ df df_from_double(double x) {
 }
 __device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
 
+// Programmatic dependent launch.  The kernels of a time step form one
+// dependent chain (sweep, rigid bodies, re-mapping passes, next sweep); each is
+// launched with programmatic stream serialisation, so it can be scheduled
+// while its predecessor is still running.  Every such kernel calls pdl_wait()
+// before it touches global memory (it returns once the predecessor grid has
+// completed and its writes are visible) and then pdl_trigger(), which lets
+// the successor be scheduled as soon as all of this grid's blocks have
+// started.  Without a programmatic predecessor pdl_wait() returns at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_enter() {
+    pdl_wait();
+    pdl_trigger();
+}
+
+template <class... KArgs, class... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // Device error-word bits.
 constexpr uint32_t ERR_NONFINITE = 1u;
 constexpr uint32_t ERR_TIMEOUT = 2u;
@@ -224,7 +262,11 @@ struct RemapArgs {
     double *wall_last;
     int nlat;
     uint32_t *err;
+    uint32_t *tbits;     // direct-sweep tile bits (may be null)
+    int tile;            // cells per direct-sweep tile
 };
+// Recount every tile bit from the flags (bit t = tile t holds a nonzero flag).
+cudaError_t launch_tile_bits(const RemapArgs &a, int ntiles, cudaStream_t s);
 cudaError_t launch_rigid_body(const RemapArgs &a, cudaStream_t s);
 cudaError_t launch_remap_step(int prec, int next_parity, const RemapArgs &a, int blocks_per_body,
                               cudaStream_t s);

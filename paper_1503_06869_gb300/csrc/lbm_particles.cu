@@ -86,37 +86,45 @@ __device__ __forceinline__ bool inside_rn(const LatDev &L, const double *pos, co
 struct BodyF32 {
     float R[9];
     float inv[3];
-    float pos[3];
+    float pos[3], poslo[3];  // centre as a double-float
 };
 
 __device__ __forceinline__ void load_body_f32(const float *src, BodyF32 &b) {
     for (int k = 0; k < 9; ++k) b.R[k] = src[BF_R + k];
     for (int k = 0; k < 3; ++k) b.inv[k] = src[BF_INV + k];
     for (int k = 0; k < 3; ++k) b.pos[k] = src[BF_POS + k];
+    for (int k = 0; k < 3; ++k) b.poslo[k] = src[BF_POSLO + k];
 }
 
-__device__ __forceinline__ float min_image_f(float d, int n, int periodic, bool &near_switch) {
+// Displacement x - x_C of a cell coordinate from a body centre held as the
+// double-float (hi, lo): formed exactly enough (|error| ~ 2^-48 |x_C|), taken
+// to the minimum image on a periodic axis, then rounded once to FP32.
+// near_switch is set when |d| is within two cells of n/2, where the image
+// choice is left to the FP64 test.
+__device__ __forceinline__ float disp_f(int x, float hi, float lo, int n, int periodic, bool &near_switch) {
+    df d = df_add_f(two_sum((float)x, -hi), -lo);
     if (periodic) {
         const float h = 0.5f * (float)n;
-        near_switch = near_switch || fabsf(fabsf(d) - h) < 2.0f;
-        if (d > h)
-            d -= (float)n;
-        else if (d < -h)
-            d += (float)n;
+        near_switch = near_switch || fabsf(fabsf(d.hi) - h) < 2.0f;
+        if (d.hi > h)
+            d = df_add_f(d, -(float)n);
+        else if (d.hi < -h)
+            d = df_add_f(d, (float)n);
     }
-    return d;
+    return d.hi;
 }
 
 // Exact inside test of the cell (i,j,k) for the body with double pose
-// (pos, quat), decided in FP32 where the FP32 value of s is far from 1; cells
-// near the periodic image switch (|d| ~ n/2) always take the FP64 test.
-__device__ __forceinline__ bool inside_fast(const LatDev &L, const double *pos, const double *quat,
+// (pos, rotation R64), decided in FP32 where the FP32 value of s is far from
+// 1; cells near the periodic image switch (|d| ~ n/2) always take the FP64
+// test.
+__device__ __forceinline__ bool inside_fast(const LatDev &L, const double *pos, const double *R64,
                                             const double *semi, const BodyF32 &b, int i, int j, int k) {
-    // d in FP64 then rounded once: |error(s)| < ~2e-4 for |d| < 100, semi-axes >= 1
+    // d rounded once from a double-float: |error(s)| < ~2e-4 for |d| < 100, semi-axes >= 1
     bool sw = false;
-    const float d0 = min_image_f((float)((double)i - pos[0]), L.nx, L.px, sw);
-    const float d1 = min_image_f((float)((double)j - pos[1]), L.ny, L.py, sw);
-    const float d2 = min_image_f((float)((double)k - pos[2]), L.nz, L.pz, sw);
+    const float d0 = disp_f(i, b.pos[0], b.poslo[0], L.nx, L.px, sw);
+    const float d1 = disp_f(j, b.pos[1], b.poslo[1], L.ny, L.py, sw);
+    const float d2 = disp_f(k, b.pos[2], b.poslo[2], L.nz, L.pz, sw);
     const float t0 = (b.R[0] * d0 + b.R[3] * d1 + b.R[6] * d2) * b.inv[0];
     const float t1 = (b.R[1] * d0 + b.R[4] * d1 + b.R[7] * d2) * b.inv[1];
     const float t2 = (b.R[2] * d0 + b.R[5] * d1 + b.R[8] * d2) * b.inv[2];
@@ -125,16 +133,17 @@ __device__ __forceinline__ bool inside_fast(const LatDev &L, const double *pos, 
         if (s < 0.999f) return true;
         if (s > 1.001f) return false;
     }
-    double R[9];
-    quat_matrix_rn(quat, R);
-    return inside_rn(L, pos, R, semi, i, j, k);
+    return inside_rn(L, pos, R64, semi, i, j, k);
 }
 
-// Half extents of the world-aligned bounding box of a rotated ellipsoid.
-__device__ __forceinline__ void aabb_half(const double R[9], const double *semi, double h[3]) {
+// Half extents of the world-aligned bounding box of a rotated ellipsoid, in
+// FP32 (the box only has to contain the body; the re-mapping region adds a
+// margin of two cells around it).
+__device__ __forceinline__ void aabb_half(const double R[9], const double *semi, float h[3]) {
     for (int a = 0; a < 3; ++a) {
-        const double e0 = R[3 * a + 0] * semi[0], e1 = R[3 * a + 1] * semi[1], e2 = R[3 * a + 2] * semi[2];
-        h[a] = sqrt(e0 * e0 + e1 * e1 + e2 * e2);
+        const float e0 = (float)R[3 * a + 0] * (float)semi[0], e1 = (float)R[3 * a + 1] * (float)semi[1],
+                    e2 = (float)R[3 * a + 2] * (float)semi[2];
+        h[a] = sqrtf(e0 * e0 + e1 * e1 + e2 * e2) * 1.0001f;
     }
 }
 
@@ -153,10 +162,15 @@ __device__ __forceinline__ double warp_sum(double v) {
 // issued up front, every store at the end, so the FP64 chain pays one memory
 // round trip instead of one per dependent access.
 __global__ void rigid_body_kernel(RemapArgs a) {
+    pdl_enter();
     static_assert(ACC_COPIES == 32, "one lane per accumulator copy");
-    const int t = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
-    if (t < a.nlat) {
+    const PartDev &P = a.P;
+    // warps [0, np) update the bodies, warps [np, np + nlat) hand over the walls
+    if (warp >= P.np) {
+        const int t = warp - P.np;
+        if (t >= a.nlat) return;
         double *w = a.wall_acc + 6 * ((size_t)t * ACC_COPIES + lane);
         double s[6];
         for (int k = 0; k < 6; ++k) s[k] = w[k];
@@ -164,9 +178,9 @@ __global__ void rigid_body_kernel(RemapArgs a) {
         for (int k = 0; k < 6; ++k) s[k] = warp_sum(s[k]);
         if (lane == 0)
             for (int k = 0; k < 6; ++k) a.wall_last[6 * t + k] = s[k];
+        return;
     }
-    const PartDev &P = a.P;
-    if (t >= P.np) return;
+    const int t = warp;
     double hs[6];  // F_h, M_h: the sweep's copies, summed
     {
         double *acc = P.acc + 6 * ((size_t)t * ACC_COPIES + lane);
@@ -188,6 +202,8 @@ __global__ void rigid_body_kernel(RemapArgs a) {
         eM[k] = P.extM[3 * t + k];
     }
     for (int k = 0; k < 4; ++k) q[k] = P.quat[4 * t + k];
+    double Rold[9];  // rotation of q, stored by the previous update
+    for (int k = 0; k < 9; ++k) Rold[k] = P.R64[9 * (size_t)t + k];
     const double minv = P.minv[t];
     const int fixed = P.fixed[t];
     const LatDev &Lt = a.lat[P.cell[t]];
@@ -208,9 +224,8 @@ __global__ void rigid_body_kernel(RemapArgs a) {
         M[k] = hs[3 + k] + eM[k];
         finite = finite && isfinite(F[k]) && isfinite(M[k]);
     }
-    double Rold[9];
-    quat_matrix_rn(q, Rold);
-    double hold[3], cold[3] = {pos[0], pos[1], pos[2]};
+    float hold[3];
+    const double cold[3] = {pos[0], pos[1], pos[2]};
     aabb_half(Rold, semi, hold);
 
     if (!fixed) {
@@ -245,7 +260,11 @@ __global__ void rigid_body_kernel(RemapArgs a) {
         nq[1] = dq[0] * q[1] + q[0] * dq[1] + (dq[2] * q[3] - dq[3] * q[2]);
         nq[2] = dq[0] * q[2] + q[0] * dq[2] + (dq[3] * q[1] - dq[1] * q[3]);
         nq[3] = dq[0] * q[3] + q[0] * dq[3] + (dq[1] * q[2] - dq[2] * q[1]);
-        const double rn = 1.0 / sqrt(nq[0] * nq[0] + nq[1] * nq[1] + nq[2] * nq[2] + nq[3] * nq[3]);
+        // renormalise: a product of unit quaternions has |nq|^2 = 1 + d with d
+        // at rounding level, and one Newton step for 1/sqrt from 1 gives
+        // 1.5 - 0.5 |nq|^2, exact to O(d^2)
+        const double n2 = nq[0] * nq[0] + nq[1] * nq[1] + nq[2] * nq[2] + nq[3] * nq[3];
+        const double rn = fabs(n2 - 1.0) < 1e-6 ? 1.5 - 0.5 * n2 : 1.0 / sqrt(n2);
         for (int k = 0; k < 4; ++k) q[k] = nq[k] * rn;
         for (int k = 0; k < 3; ++k)
             if (per[k]) {
@@ -265,30 +284,38 @@ __global__ void rigid_body_kernel(RemapArgs a) {
     }
     if (!finite) atomicOr(a.err, ERR_NONFINITE);
 
-    // re-mapping box: union of old and new bounding boxes, margin 2 cells
-    double Rnew[9], hnew[3];
+    // rotation of the new orientation, rounded as the mapping's exact inside
+    // test expects; FP32 copies of the new pose and motion for the
+    // re-mapping pre-test and the sweep's bounce-back (reciprocal semi-axes
+    // are set once, on the host)
+    double Rnew[9];
     quat_matrix_rn(q, Rnew);
+    for (int k = 0; k < 9; ++k) P.R64[9 * (size_t)t + k] = Rnew[k];
+    float hnew[3];
     aabb_half(Rnew, semi, hnew);
-    // FP32 copy of the new pose and motion for the re-mapping pre-test and
-    // the sweep's bounce-back (reciprocal semi-axes are set once, on the host)
     float *bf = P.bodyf + BF_STRIDE * (size_t)t;
     for (int k = 0; k < 9; ++k) bf[BF_R + k] = (float)Rnew[k];
+    float posf[3], coldf[3];
     for (int k = 0; k < 3; ++k) {
         const df c = df_from_double(pos[k]);
         bf[BF_POS + k] = c.hi;
         bf[BF_POSLO + k] = c.lo;
         bf[BF_U + k] = (float)vel[k];
         bf[BF_W + k] = (float)om[k];
+        posf[k] = c.hi;
+        coldf[k] = (float)cold[k];
     }
+    // re-mapping box: union of the old and new bounding boxes plus a margin
+    // of two cells, in FP32 with a slack far above its rounding
     for (int k = 0; k < 3; ++k) {
-        double lo = fmin(cold[k] - hold[k], pos[k] - hnew[k]);
-        double hi = fmax(cold[k] + hold[k], pos[k] + hnew[k]);
+        float lo = fminf(coldf[k] - hold[k], posf[k] - hnew[k]) - 1e-3f;
+        float hi = fmaxf(coldf[k] + hold[k], posf[k] + hnew[k]) + 1e-3f;
         // a wrapped centre makes the two boxes an image apart: use the new one
-        if (per[k] && fabs(cold[k] - pos[k]) > 0.5 * dims[k]) {
-            lo = fmin(pos[k] - hnew[k], pos[k] - hold[k]);
-            hi = fmax(pos[k] + hnew[k], pos[k] + hold[k]);
+        if (per[k] && fabsf(coldf[k] - posf[k]) > 0.5f * (float)dims[k]) {
+            lo = fminf(posf[k] - hnew[k], posf[k] - hold[k]) - 1e-3f;
+            hi = fmaxf(posf[k] + hnew[k], posf[k] + hold[k]) + 1e-3f;
         }
-        int ilo = (int)floor(lo) - 2, ihi = (int)ceil(hi) + 2;
+        int ilo = (int)floorf(lo) - 2, ihi = (int)ceilf(hi) + 2;
         if (!isfinite(lo) || !isfinite(hi)) { ilo = 0; ihi = -1; }
         if (per[k]) {
             if (ihi - ilo + 1 > dims[k]) { ilo = 0; ihi = dims[k] - 1; }
@@ -341,6 +368,7 @@ __device__ __forceinline__ RegionLoop region_loop(int bpb) {
 
 template <int PASS>
 __global__ void remap_region_kernel(RemapArgs a, int bpb) {
+    pdl_enter();
     const RegionLoop rl = region_loop(bpb);
     const int p = rl.p;
     const PartDev &P = a.P;
@@ -349,7 +377,7 @@ __global__ void remap_region_kernel(RemapArgs a, int bpb) {
     const int vol = reg[3] * reg[4] * reg[5];
     if (vol <= 0) return;
     const LatDev &L = a.lat[P.cell[p]];
-    const double *pos = P.pos + 3 * p, *semi = P.semi + 3 * p, *quat = P.quat + 4 * p;
+    const double *pos = P.pos + 3 * p, *semi = P.semi + 3 * p, *R64 = P.R64 + 9 * (size_t)p;
     BodyF32 bf;
     load_body_f32(P.bodyf + BF_STRIDE * (size_t)p, bf);
     for (int r = rl.first; r < vol; r += rl.stride) {
@@ -357,13 +385,13 @@ __global__ void remap_region_kernel(RemapArgs a, int bpb) {
         region_cell(reg, L, r, c);
         const long long cg = L.c_off + c.idx;
         if (PASS == 0) {  // uncover
-            if (a.pid[cg] == (uint32_t)p && !inside_fast(L, pos, quat, semi, bf, c.i, c.j, c.k)) {
+            if (a.pid[cg] == (uint32_t)p && !inside_fast(L, pos, R64, semi, bf, c.i, c.j, c.k)) {
                 a.pid[cg] = PID_FLUID;
                 a.pid_prev[cg] = (uint32_t)p;
                 a.flags[cg] |= F_CHANGED;
             }
         } else {  // claim
-            if (!(a.flags[cg] & F_WALL) && inside_fast(L, pos, quat, semi, bf, c.i, c.j, c.k)) {
+            if (!(a.flags[cg] & F_WALL) && inside_fast(L, pos, R64, semi, bf, c.i, c.j, c.k)) {
                 const uint32_t old = atomicMin(&a.pid[cg], (uint32_t)p);
                 if (old == PID_FLUID) a.flags[cg] |= F_CHANGED;
             }
@@ -466,6 +494,7 @@ __device__ void fixup_cell(const RemapArgs &a, const LatDev &L, int i, int j, in
 
 template <int PREC, int NEXT_ODD>
 __global__ void fixup_region_kernel(RemapArgs a, int bpb) {
+    pdl_enter();
     const RegionLoop rl = region_loop(bpb);
     const int p = rl.p;
     const PartDev &P = a.P;
@@ -516,6 +545,7 @@ __device__ __forceinline__ uint8_t flag_of(const LatDev &L, const uint32_t *pid,
 }
 
 __global__ void flags_region_kernel(RemapArgs a, int bpb) {
+    pdl_enter();
     const RegionLoop rl = region_loop(bpb);
     const int p = rl.p;
     const PartDev &P = a.P;
@@ -530,7 +560,42 @@ __global__ void flags_region_kernel(RemapArgs a, int bpb) {
         if (a.flags[cg] & F_WALL) continue;
         const uint8_t f = flag_of(L, a.pid, L.c_off, c.i, c.j, c.k);
         a.flags[cg] = f;
+        // a cell turning non-bulk marks its tile; marks are cleared only by a
+        // recount (launch_tile_bits), so a stale mark costs the flagged path,
+        // never a missed cell
+        if (f && a.tbits) {
+            const int t = L.tile0 + c.idx / a.tile;
+            atomicOr(a.tbits + (t >> 5), 1u << (t & 31));
+        }
     }
+}
+
+// One block per 32 tiles (one word of tile bits); warp w scans tiles w, w+8,
+// w+16, w+24 of the word.
+__global__ void tile_bits_kernel(RemapArgs a, int ntiles) {
+    pdl_enter();
+    __shared__ uint32_t word;
+    if (threadIdx.x == 0) word = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int j = warp; j < 32; j += 8) {
+        const int tile = blockIdx.x * 32 + j;
+        if (tile >= ntiles) break;
+        int lo = 0, hi = a.nlat - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.lat[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
+        }
+        const LatDev &L = a.lat[lo];
+        bool any = false;
+        for (int c = lane; c < a.tile; c += 32) {
+            const int idx = (tile - L.tile0) * a.tile + c;
+            if (idx < L.n && a.flags[L.c_off + idx]) any = true;
+        }
+        if (__any_sync(0xffffffffu, any) && lane == 0) atomicOr(&word, 1u << j);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) a.tbits[blockIdx.x] = word;
 }
 
 // ---------------------------------------------------------------------------
@@ -749,14 +814,13 @@ constexpr int REMAP_BLOCK = 256;
 template <int PREC>
 cudaError_t remap_step_prec(int next_parity, const RemapArgs &a, int bpb, cudaStream_t s) {
     const unsigned grid = (unsigned)bpb * (unsigned)a.P.np;
-    remap_region_kernel<0><<<grid, REMAP_BLOCK, 0, s>>>(a, bpb);
-    remap_region_kernel<1><<<grid, REMAP_BLOCK, 0, s>>>(a, bpb);
-    if (next_parity)
-        fixup_region_kernel<PREC, 1><<<grid, REMAP_BLOCK, 0, s>>>(a, bpb);
-    else
-        fixup_region_kernel<PREC, 0><<<grid, REMAP_BLOCK, 0, s>>>(a, bpb);
-    flags_region_kernel<<<grid, REMAP_BLOCK, 0, s>>>(a, bpb);
-    return cudaGetLastError();
+    cudaError_t e = launch_pdl(remap_region_kernel<0>, grid, REMAP_BLOCK, 0, s, a, bpb);
+    if (e == cudaSuccess) e = launch_pdl(remap_region_kernel<1>, grid, REMAP_BLOCK, 0, s, a, bpb);
+    if (e == cudaSuccess)
+        e = next_parity ? launch_pdl(fixup_region_kernel<PREC, 1>, grid, REMAP_BLOCK, 0, s, a, bpb)
+                        : launch_pdl(fixup_region_kernel<PREC, 0>, grid, REMAP_BLOCK, 0, s, a, bpb);
+    if (e == cudaSuccess) e = launch_pdl(flags_region_kernel, grid, REMAP_BLOCK, 0, s, a, bpb);
+    return e;
 }
 
 template <int PREC>
@@ -798,11 +862,15 @@ cudaError_t set_pdfs_prec(int next_parity, const LatDev &h, const LatDev *d, voi
 
 int kernels_per_remap_step() { return 4; }
 
+cudaError_t launch_tile_bits(const RemapArgs &a, int ntiles, cudaStream_t s) {
+    if (!a.tbits || ntiles <= 0) return cudaSuccess;
+    return launch_pdl(tile_bits_kernel, (ntiles + 31) / 32, 256, 0, s, a, ntiles);
+}
+
 cudaError_t launch_rigid_body(const RemapArgs &a, cudaStream_t s) {
-    const int n = a.P.np > a.nlat ? a.P.np : a.nlat;
+    const int n = a.P.np + a.nlat;  // one warp per body, then one per lattice
     if (n <= 0) return cudaSuccess;
-    rigid_body_kernel<<<(int)((32ll * n + 127) / 128), 128, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(rigid_body_kernel, (int)((32ll * n + 127) / 128), 128, 0, s, a);
 }
 
 #define LBM_DISPATCH(prec, call)                                        \

@@ -581,12 +581,14 @@ __device__ __noinline__ void wall_cell(const SweepArgs &a, const LatDev &L, int 
 
 // Fluid cell with fluid neighbours only.
 template <int PREC, int ODD>
-__device__ __forceinline__ void bulk_cell(const SweepArgs &a, const LatDev &L, int idx, const CellGeom &cg) {
+__device__ __forceinline__ void bulk_cell(const SweepArgs &a, const LatDev &L, int idx) {
     using S = Store<PREC>;
     using T = typename S::T;
     using C = typename S::C;
     T *base = reinterpret_cast<T *>(a.f) + L.f_off;
     const long long np = L.npad;
+    CellGeom cg;
+    if (ODD) cg = cell_geom(L, idx);
     C g[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
@@ -649,6 +651,7 @@ __device__ __forceinline__ void flush_forces(const SweepArgs &a, uint32_t *tkey,
 template <int PREC, int ODD, bool SINGLE>
 __global__ void __launch_bounds__(256, SweepBounds<PREC>::MINB)
     sweep_kernel(const __grid_constant__ SweepArgs a) {
+    pdl_enter();
     using S = Store<PREC>;
     using T = typename S::T;
     using C = typename S::C;
@@ -661,6 +664,11 @@ __global__ void __launch_bounds__(256, SweepBounds<PREC>::MINB)
         const LatDev &L = SINGLE ? a.lat0 : a.lat[li];
         const int idx = (tile - L.tile0) * blockDim.x + threadIdx.x;
         if (idx >= L.n) continue;
+        if (a.tbits && !((a.tbits[tile >> 5] >> (tile & 31)) & 1u)) {
+            // a tile of bulk fluid cells only (uniform per block): no flag read
+            bulk_cell<PREC, ODD>(a, L, idx);
+            continue;
+        }
         T *base = reinterpret_cast<T *>(a.f) + L.f_off;
         const long long np = L.npad;
         // the 19 populations are read at the bulk pull addresses, which are in
@@ -811,6 +819,7 @@ __device__ __forceinline__ void bulk_cell_staged(const SweepArgs &a, const LatDe
 template <int PREC, int ODD, bool SINGLE>
 __global__ void __launch_bounds__(256, SweepBounds<PREC>::MINB)
     sweep_staged(const __grid_constant__ SweepArgs a) {
+    pdl_enter();
     using S = Store<PREC>;
     using T = typename S::T;
     using Cfg = StageCfg<PREC>;
@@ -887,7 +896,7 @@ __global__ void __launch_bounds__(256, SweepBounds<PREC>::MINB)
                             else
                                 near_cell<PREC, ODD, 0>(a, L, li, idx, &tkey[tid], tval[tid], nullptr);
                         } else {
-                            bulk_cell<PREC, ODD>(a, L, idx, cg);
+                            bulk_cell<PREC, ODD>(a, L, idx);
                         }
                     }
                 }
@@ -964,6 +973,7 @@ __device__ __forceinline__ void ring_fetch(const SweepArgs &a, const LatDev &L, 
 template <int PREC, int ODD, bool SINGLE>
 __global__ void __launch_bounds__(256, SweepBounds<PREC>::MINB)
     sweep_ring(const __grid_constant__ SweepArgs a) {
+    pdl_enter();
     using S = Store<PREC>;
     using T = typename S::T;
     using C = typename S::C;
@@ -1048,7 +1058,7 @@ cudaError_t launch_one(int variant, const SweepArgs &a, int grid, int block, cud
             if (e != cudaSuccess) return e;
             attr = true;
         }
-        sweep_staged<PREC, ODD, SINGLE><<<grid, StageCfg<PREC>::TILE, smem, s>>>(a);
+        return launch_pdl(sweep_staged<PREC, ODD, SINGLE>, grid, StageCfg<PREC>::TILE, smem, s, a);
     } else if (variant == SWEEP_RING) {
         constexpr int smem = RingCfg<PREC>::SMEM;
         static bool attr = false;
@@ -1058,11 +1068,10 @@ cudaError_t launch_one(int variant, const SweepArgs &a, int grid, int block, cud
             if (e != cudaSuccess) return e;
             attr = true;
         }
-        sweep_ring<PREC, ODD, SINGLE><<<grid, RingCfg<PREC>::TILE, smem, s>>>(a);
+        return launch_pdl(sweep_ring<PREC, ODD, SINGLE>, grid, RingCfg<PREC>::TILE, smem, s, a);
     } else {
-        sweep_kernel<PREC, ODD, SINGLE><<<grid, block, 0, s>>>(a);
+        return launch_pdl(sweep_kernel<PREC, ODD, SINGLE>, grid, block, 0, s, a);
     }
-    return cudaGetLastError();
 }
 
 template <int PREC>
