@@ -395,6 +395,15 @@ lbm_status create_common(const lbm_grid_desc *cells, int ncells, lbm_ctx **out) 
             L.whi[a] = d.wall_u_hi[a];
             L.g[a] = d.body_force[a];
         }
+        L.fomega = (float)L.omega;
+        L.fomega_odd = (float)L.omega_odd;
+        L.frho0 = (float)L.rho0;
+        L.finv_rho0 = (float)L.inv_rho0;
+        for (int a = 0; a < 3; ++a) {
+            L.fg[a] = (float)L.g[a];
+            L.fwlo[a] = (float)L.wlo[a];
+            L.fwhi[a] = (float)L.whi[a];
+        }
         for (int q = 0; q < Q; ++q) L.off[q] = cx(q) + cy(q) * d.nx + cz(q) * d.nx * d.ny;
         foff += (long long)Q * L.npad;
         coff += (L.n + 255) / 256 * 256;

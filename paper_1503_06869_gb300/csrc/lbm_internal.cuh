@@ -84,7 +84,27 @@ struct LatDev {
     double rho18;          // rho0 / 18: 2 w_q rho0 = (36 w_q) rho0 / 18 with 36 w_q in {1, 2}
     double wlo[3], whi[3], g[3];
     float rho18f[2];       // rho0 / 18 as a double-float (hi, lo)
+    // FP32 copies of the relaxation and boundary parameters: a double -> float
+    // conversion issues on GB300's narrow FP64 pipe, so the FP32/FP16/BF16
+    // sweeps read these instead of converting per cell
+    float fomega, fomega_odd, frho0, finv_rho0;
+    float fg[3], fwlo[3], fwhi[3];
     int off[Q];            // linear offset of x + c_q for cells off the periodic faces
+};
+
+// Lattice parameters in the compute precision C (FP64 fields for double, the
+// FP32 copies otherwise).
+template <class C> struct LatPar {
+    C omega, omega_odd, rho0, inv_rho0, g[3], wlo[3], whi[3];
+    __device__ __forceinline__ explicit LatPar(const LatDev &L) {
+        if constexpr (sizeof(C) == 8) {
+            omega = L.omega; omega_odd = L.omega_odd; rho0 = L.rho0; inv_rho0 = L.inv_rho0;
+            for (int k = 0; k < 3; ++k) { g[k] = L.g[k]; wlo[k] = L.wlo[k]; whi[k] = L.whi[k]; }
+        } else {
+            omega = L.fomega; omega_odd = L.fomega_odd; rho0 = L.frho0; inv_rho0 = L.finv_rho0;
+            for (int k = 0; k < 3; ++k) { g[k] = L.fg[k]; wlo[k] = L.fwlo[k]; whi[k] = L.fwhi[k]; }
+        }
+    }
 };
 
 // Rigid bodies, structure of arrays, FP64 throughout.

@@ -99,6 +99,12 @@ __device__ __forceinline__ void collide(C (&g)[Q], C om, C oo, C rho0, C inv, C 
     }
 }
 
+template <class C>
+__device__ __forceinline__ void collide_lat(C (&g)[Q], const LatDev &L) {
+    const LatPar<C> p(L);
+    collide<C>(g, p.omega, p.omega_odd, p.rho0, p.inv_rho0, p.g[0], p.g[1], p.g[2]);
+}
+
 struct CellGeom {
     int x, y, z;
     int dxm, dxp, dym, dyp, dzm, dzp;  // neighbour offsets with periodic wrap
@@ -455,13 +461,14 @@ __device__ __noinline__ void near_cell(const SweepArgs &a, const LatDev &L, int 
             }
         }
     }
-    collide<C>(g, C(L.omega), C(L.omega_odd), C(L.rho0), C(L.inv_rho0), C(L.g[0]), C(L.g[1]), C(L.g[2]));
+    collide_lat<C>(g, L);
     // Wall links are bounced inline as well: the wall layer that is hit
     // follows from the neighbour's y (a y = 0 or y = ny-1 layer of a
     // non-periodic y axis moves, any other wall layer rests).
     LinkSum<C> lw, lb;
     int wside = -1;
-    const C rho0c = C(L.rho0);
+    const LatPar<C> lp(L);
+    const C rho0c = lp.rho0;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         if ((wall >> q) & 1u) {
@@ -470,10 +477,10 @@ __device__ __noinline__ void near_cell(const SweepArgs &a, const LatDev &L, int 
             C u0 = 0, u1 = 0, u2 = 0;
             if (!L.py && ys == 0) {
                 side = 0;
-                u0 = C(L.wlo[0]); u1 = C(L.wlo[1]); u2 = C(L.wlo[2]);
+                u0 = lp.wlo[0]; u1 = lp.wlo[1]; u2 = lp.wlo[2];
             } else if (!L.py && ys == L.ny - 1) {
                 side = 1;
-                u0 = C(L.whi[0]); u1 = C(L.whi[1]); u2 = C(L.whi[2]);
+                u0 = lp.whi[0]; u1 = lp.whi[1]; u2 = lp.whi[2];
             }
             C cu = 0;
             if (cx(q)) cu += cx(q) > 0 ? u0 : -u0;
@@ -554,9 +561,10 @@ __device__ __noinline__ void wall_cell(const SweepArgs &a, const LatDev &L, int 
 #pragma unroll
         for (int q = 0; q < Q; ++q) g[q] = S::ld(base + q * np + idx);
     }
-    collide<C>(g, C(L.omega), C(L.omega_odd), C(L.rho0), C(L.inv_rho0), C(L.g[0]), C(L.g[1]), C(L.g[2]));
-    const double *uw = SIDE == 0 ? L.wlo : L.whi;
-    const C u0 = C(uw[0]), u1 = C(uw[1]), u2 = C(uw[2]), rho0c = C(L.rho0);
+    collide_lat<C>(g, L);
+    const LatPar<C> lp(L);
+    const C *uw = SIDE == 0 ? lp.wlo : lp.whi;
+    const C u0 = uw[0], u1 = uw[1], u2 = uw[2], rho0c = lp.rho0;
     LinkSum<C> lw;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
@@ -597,7 +605,7 @@ __device__ __forceinline__ void bulk_cell(const SweepArgs &a, const LatDev &L, i
         else
             g[q] = S::ld(base + opp(q) * np + idx + nb_off(cg, opp(q)));
     }
-    collide<C>(g, C(L.omega), C(L.omega_odd), C(L.rho0), C(L.inv_rho0), C(L.g[0]), C(L.g[1]), C(L.g[2]));
+    collide_lat<C>(g, L);
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         if (!ODD)
@@ -696,7 +704,7 @@ __global__ void __launch_bounds__(256, SweepBounds<PREC>::MINB)
             near_cell<PREC, ODD, 0>(a, L, li, idx, &tkey[threadIdx.x], tval[threadIdx.x], nullptr);
             continue;
         }
-        collide<C>(g, C(L.omega), C(L.omega_odd), C(L.rho0), C(L.inv_rho0), C(L.g[0]), C(L.g[1]), C(L.g[2]));
+        collide_lat<C>(g, L);
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
             if (!ODD)
@@ -806,7 +814,7 @@ __device__ __forceinline__ void bulk_cell_staged(const SweepArgs &a, const LatDe
 #pragma unroll
     for (int q = 0; q < Q; ++q)
         g[q] = S::ld(stage + q * Cfg::W + (ODD ? (L.off[opp(q)] & (Cfg::A - 1)) : 0) + threadIdx.x);
-    collide<C>(g, C(L.omega), C(L.omega_odd), C(L.rho0), C(L.inv_rho0), C(L.g[0]), C(L.g[1]), C(L.g[2]));
+    collide_lat<C>(g, L);
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         if (!ODD)
@@ -1030,7 +1038,7 @@ __global__ void __launch_bounds__(256, SweepBounds<PREC>::MINB)
 #pragma unroll
         for (int q = 0; q < Q; ++q)
             g[q] = ring_value<PREC>(col, q, ODD ? ((idx + nb_off(cg, opp(q))) & 1) : (idx & 1));
-        collide<C>(g, C(L.omega), C(L.omega_odd), C(L.rho0), C(L.inv_rho0), C(L.g[0]), C(L.g[1]), C(L.g[2]));
+        collide_lat<C>(g, L);
         T *base = reinterpret_cast<T *>(a.f) + L.f_off;
         const long long np = L.npad;
 #pragma unroll
