@@ -33,6 +33,33 @@ from lbm_inputs import large_shear, small_shear, batched_shear  # noqa: E402
 
 BYTES_PER_POP = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
 
+# DRAM traffic per sweep launch (dram__bytes_read.sum + dram__bytes_write.sum,
+# mean of one even and one odd launch) from an ncu capture of the sweep
+# kernel, keyed by workload and precision, with the fingerprint of the sweep
+# sources it was taken on; a changed kernel reports no traffic until it is
+# captured again.  Captures are summarised under profiles/.
+SWEEP_SOURCES = ("paper_1503_06869_gb300/csrc/lbm_sweep.cu", "paper_1503_06869_gb300/csrc/lbm_internal.cuh")
+SWEEP_TRAFFIC = {
+    ("shear256x128x128_spheroid24x3x3", "f32"): {"bytes": 577.86e6, "src": "a1427aab7c7d18ca",
+                                                "profile": "profiles/sweep_kernel_shear256x128x128_f32.md"},
+}
+
+
+def sweep_fingerprint() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in SWEEP_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def sweep_traffic(workload_name: str, prec: str):
+    rec = SWEEP_TRAFFIC.get((workload_name, prec))
+    if rec is None or rec["src"] != sweep_fingerprint():
+        return None
+    return rec["bytes"]
+
 
 def workload(name: str):
     if name == "large":
@@ -261,7 +288,7 @@ def main():
     sweep_avg_ms = sweep_ms / max(sweep_n, 1)
     achieved = bytes_per_launch / (sweep_avg_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": None,
+            "frac": round(achieved / peak, 4), "traffic": sweep_traffic(w.name, args.prec),
             "kernel": "sweep_kernel", "bytes_per_launch": bytes_per_launch,
             "avg_launch_ms": round(sweep_avg_ms, 5), "peak_kind": f"{peak_kind} hbm_gbs"}
 
