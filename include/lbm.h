@@ -259,6 +259,79 @@ lbm_status lbm_get_sweep_timing(lbm_ctx *ctx, double *ms, long long *launches);
 /* Number of kernel launches issued by the library since creation. */
 lbm_status lbm_get_launch_count(lbm_ctx *ctx, long long *launches);
 
+/* ---------------------------------------------------------------------------
+ * Learned force/torque closure.  The paper has none: its force and torque
+ * are the momentum exchange of Eqs. TransferredMomentum / LBMhydrodynForce
+ * (Sec. 4.2), applied in the rigid-body update (Sec. 4.3).  A closure adds a
+ * correction predicted by a 86-64-64-64-6 ReLU network from the flow around
+ * each body, before that update.
+ *
+ * Features (LBM_CLOSURE_IN per body): 27 sample points in the body frame at
+ * offsets (1.5a i, 1.5b j, 1.5c k), i,j,k in {-1,0,1}, point s = 9(i+1) +
+ * 3(j+1) + (k+1), (a,b,c) the semi-axes; at the world point x_C + R o_s the
+ * velocity field (as lbm_get_fields reports it: zero on wall and particle
+ * cells) is interpolated trilinearly between cell centres (periodic axes
+ * wrap, the others clamp to the lattice); feature 3s+d is component d of
+ * R^T (u - U) / V, U the body velocity, V = gamma * a.  Features 81..83: the
+ * body x axis in world coordinates (first column of R); 84: a/b; 85: b.
+ * gamma is the shear rate of the channel between the moving y walls,
+ * |u_hi,x - u_lo,x| / (ny - 2); a lattice without moving y walls has gamma
+ * = 0 (V = 1) and its bodies get no correction.
+ *
+ * Network parameters: one flat vector of LBM_CLOSURE_PARAMS values, W1 (64 x
+ * 86, row-major [out][in]), b1 (64), W2 (64 x 64), b2, W3 (64 x 64), b3, W4
+ * (6 x 64), b4 (6); ReLU after the three hidden layers.  Outputs o: the
+ * body-frame correction dF = o[0..2] * mu gamma a b, dM = o[3..5] *
+ * mu gamma a^2 b, mu = rho0 (tau - 1/2) / 3, rotated to the world frame.
+ * Inference runs on the FP16 tensor cores with FP32 accumulation.
+ * ------------------------------------------------------------------------- */
+#define LBM_CLOSURE_IN 86
+#define LBM_CLOSURE_OUT 6
+#define LBM_CLOSURE_PARAMS 14278
+
+/* Enable the closure with FP16 parameters (host array of LBM_CLOSURE_PARAMS
+ * IEEE half values, bytes = 2 * LBM_CLOSURE_PARAMS), or disable it (params =
+ * NULL).  While enabled every time step evaluates the network after the
+ * sweep and adds the correction to the force and torque of every body; the
+ * forces lbm_get_forces reports then include the correction.  Synchronises
+ * the stream.  Errors: LBM_ERR_ARG for a wrong size. */
+lbm_status lbm_set_closure(lbm_ctx *ctx, const void *params, size_t bytes);
+
+/* Features of every body in the current state (the velocity field the next
+ * sweep starts from, the bodies' current pose and velocity): n x
+ * LBM_CLOSURE_IN floats into the host array features; n must equal the
+ * number of bodies.  Synchronises the stream. */
+lbm_status lbm_closure_features(lbm_ctx *ctx, float *features, int n);
+
+/* Training of the closure network on the GPU.  An lbm_mlp holds FP32 master
+ * parameters, the Adam moments and an FP16 working copy in device memory
+ * (cudaMalloc, released by lbm_mlp_destroy); its work is ordered on the given
+ * CUDA stream (NULL: the legacy default stream).  Samples are device arrays:
+ * x (n x LBM_CLOSURE_IN floats), y (n x LBM_CLOSURE_OUT floats).  Loss: the
+ * mean over samples and outputs of (o - y)^2.  The forward and backward
+ * passes run on the FP16 tensor cores with FP32 accumulation; the output
+ * delta is kept unscaled (o - y) in FP16 and the factor 2/(6n) is applied to
+ * the FP32 gradient. */
+typedef struct lbm_mlp lbm_mlp;
+
+/* Create a trainer from initial FP32 parameters (host, LBM_CLOSURE_PARAMS). */
+lbm_status lbm_mlp_create(const float *params, void *cuda_stream, lbm_mlp **out);
+/* Network outputs for n samples: y (device, n x LBM_CLOSURE_OUT floats). */
+lbm_status lbm_mlp_forward(lbm_mlp *m, const float *x, float *y, int n);
+/* Loss and gradient over n samples without changing the parameters: grad
+ * (device, LBM_CLOSURE_PARAMS floats, may be NULL) and loss (host, may be
+ * NULL; synchronises). */
+lbm_status lbm_mlp_grad(lbm_mlp *m, const float *x, const float *y, int n, float *grad, float *loss);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on the
+ * gradient over the n samples; loss (host, may be NULL; synchronises)
+ * receives the loss before the step. */
+lbm_status lbm_mlp_train_step(lbm_mlp *m, const float *x, const float *y, int n, float lr, float *loss);
+/* Current parameters: FP32 master values (host, may be NULL) and the FP16
+ * copy lbm_set_closure takes (host, 2 * LBM_CLOSURE_PARAMS bytes, may be
+ * NULL).  Synchronises. */
+lbm_status lbm_mlp_get_params(lbm_mlp *m, float *params, void *params_fp16);
+lbm_status lbm_mlp_destroy(lbm_mlp *m);
+
 lbm_status lbm_destroy(lbm_ctx *ctx);
 const char *lbm_last_error(const lbm_ctx *ctx);
 const char *lbm_status_string(lbm_status s);

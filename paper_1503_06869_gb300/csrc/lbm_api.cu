@@ -38,6 +38,8 @@ struct lbm_ctx {
     uint32_t *pid = nullptr, *pid_prev = nullptr;
     double *wall_acc = nullptr, *wall_last = nullptr;
     uint32_t *tbits = nullptr;      // direct sweep: tiles that may hold non-bulk cells
+    __half *cl_par = nullptr;       // learned closure: FP16 network parameters
+    bool closure = false;
     uint32_t *err = nullptr;
 
     int np = 0;
@@ -194,6 +196,26 @@ RemapArgs remap_args(lbm_ctx *ctx) {
     return a;
 }
 
+ClosureArgs closure_args(lbm_ctx *ctx) {
+    ClosureArgs a{};
+    a.lat = ctx->lat_d;
+    a.f = ctx->f;
+    a.flags = ctx->flags;
+    a.P = ctx->P;
+    a.feat = ctx->P.feat;
+    return a;
+}
+
+MlpArgs closure_mlp_args(lbm_ctx *ctx) {
+    MlpArgs m{};
+    m.par16 = ctx->cl_par;
+    m.x = ctx->P.feat;
+    m.n = ctx->np;
+    return m;
+}
+
+int closure_kernels(const lbm_ctx *ctx) { return (ctx->closure && ctx->np > 0) ? 2 : 0; }
+
 // Recount the direct sweep's tile bits from the flags (clears stale marks).
 lbm_status recount_tiles(lbm_ctx *ctx) {
     if (ctx->variant != SWEEP_DIRECT) return LBM_OK;
@@ -235,6 +257,14 @@ lbm_status enqueue_step(lbm_ctx *ctx, bool timed) {
         CK(cudaEventRecord(ctx->ev[ctx->ev_used + 1], ctx->stream));
         ctx->ev_used += 2;
         ctx->timed_launches += 1;
+    }
+    if (ctx->closure && ctx->np > 0) {
+        // learned closure: features after the sweep, network, correction
+        // added to the bodies' accumulators before their update
+        const ClosureArgs ca = closure_args(ctx);
+        CK(launch_closure_features(ctx->prec, 1 - parity, ca, ctx->stream));
+        CK(launch_mlp_infer(closure_mlp_args(ctx), &ca, ctx->stream));
+        ctx->launches += 2;
     }
     RemapArgs ra = remap_args(ctx);
     CK(launch_rigid_body(ra, ctx->stream));
@@ -395,6 +425,9 @@ lbm_status create_common(const lbm_grid_desc *cells, int ncells, lbm_ctx **out) 
             L.whi[a] = d.wall_u_hi[a];
             L.g[a] = d.body_force[a];
         }
+        // learned closure scales: shear rate between moving y walls, viscosity
+        L.cl_gamma = d.periodic[1] ? 0.0f : (float)(std::fabs(d.wall_u_hi[0] - d.wall_u_lo[0]) / (d.ny - 2.0));
+        L.cl_mu = (float)(d.rho0 * (d.tau - 0.5) / 3.0);
         L.fomega = (float)L.omega;
         L.fomega_odd = (float)L.omega_odd;
         L.frho0 = (float)L.rho0;
@@ -617,6 +650,7 @@ lbm_status lbm_set_particles(lbm_ctx *ctx, const lbm_particle *p, int n) {
     P.Iinv = part_alloc<double>(ctx, 3 * m);
     P.bodyf = part_alloc<float>(ctx, BF_STRIDE * m);
     P.R64 = part_alloc<double>(ctx, 9 * m);
+    P.feat = part_alloc<float>(ctx, (size_t)CL_IN * m);
     P.extF = part_alloc<double>(ctx, 3 * m);
     P.extM = part_alloc<double>(ctx, 3 * m);
     P.cell = part_alloc<int>(ctx, m);
@@ -699,7 +733,7 @@ lbm_status lbm_step(lbm_ctx *ctx, int nsteps) {
                 lbm_status s = build_graph(ctx);
                 if (s != LBM_OK) return s;
             }
-            const int per = 2 * (2 + (ctx->np > 0 ? kernels_per_remap_step() : 0));
+            const int per = 2 * (2 + closure_kernels(ctx) + (ctx->np > 0 ? kernels_per_remap_step() : 0));
             while (left >= 2) {
                 CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
                 ctx->t += 2;
@@ -1066,6 +1100,38 @@ lbm_status lbm_get_sweep_timing(lbm_ctx *ctx, double *ms, long long *launches) {
 lbm_status lbm_get_launch_count(lbm_ctx *ctx, long long *launches) {
     if (!ctx || !launches) return LBM_ERR_ARG;
     *launches = ctx->launches;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_closure(lbm_ctx *ctx, const void *params, size_t bytes) {
+    if (!ctx) return LBM_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->stream));
+    drop_graph(ctx);  // the captured step changes with the closure
+    if (!params) {
+        ctx->closure = false;
+        return LBM_OK;
+    }
+    if (bytes != sizeof(__half) * CL_PARAMS)
+        return fail(ctx, LBM_ERR_ARG, "closure parameters must be LBM_CLOSURE_PARAMS half values");
+    if (!ctx->cl_par) {
+        ctx->cl_par = (__half *)owned_alloc(ctx, sizeof(__half) * CL_PARAMS);
+        if (!ctx->cl_par) return fail(ctx, LBM_ERR_OOM, "closure parameters");
+    }
+    CK(cudaMemcpyAsync(ctx->cl_par, params, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->closure = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_closure_features(lbm_ctx *ctx, float *features, int n) {
+    if (!ctx) return LBM_ERR_ARG;
+    if (n != ctx->np || (n > 0 && !features)) return fail(ctx, LBM_ERR_ARG, "n must equal the number of bodies");
+    if (n == 0) return LBM_OK;
+    CK(launch_closure_features(ctx->prec, (int)(ctx->t & 1), closure_args(ctx), ctx->stream));
+    ctx->launches += 1;
+    CK(cudaMemcpyAsync(features, ctx->P.feat, sizeof(float) * CL_IN * (size_t)n, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
     return LBM_OK;
 }
 

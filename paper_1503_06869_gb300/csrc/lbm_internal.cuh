@@ -89,6 +89,9 @@ struct LatDev {
     // sweeps read these instead of converting per cell
     float fomega, fomega_odd, frho0, finv_rho0;
     float fg[3], fwlo[3], fwhi[3];
+    // learned closure scales: shear rate of the channel between the moving
+    // y walls (0 without them: no closure) and dynamic viscosity
+    float cl_gamma, cl_mu;
     int off[Q];            // linear offset of x + c_q for cells off the periodic faces
 };
 
@@ -116,6 +119,7 @@ struct PartDev {
     double *minv, *Iinv;                 // 1/mass, 1/inertia (host-computed)
     float *bodyf;                        // BF_STRIDE per body, layout BF_* below
     double *R64;                         // 9 per body: rotation of quat, rounded as the mapping's inside test
+    float *feat;                         // learned closure: features, CL_IN per body
     double *extF, *extM;                 // external loads
     int *cell, *fixed;
     double *pos_old, *vel_old, *om_old, *quat_old; // state before this step's update
@@ -268,6 +272,34 @@ constexpr int SWEEP_STAGED = 1;
 constexpr int SWEEP_RING = 2;
 cudaError_t launch_sweep(int prec, int parity, int variant, const SweepArgs &a, int grid, int block,
                          cudaStream_t s);
+
+// Learned closure (see lbm_closure.cu): features of every body, network
+// inference (applied to the bodies' accumulators, or written out), training.
+constexpr int CL_IN = 86, CL_HID = 64, CL_OUT = 6, CL_PARAMS = 14278;
+struct ClosureArgs {
+    const LatDev *lat;
+    const void *f;
+    const uint8_t *flags;
+    PartDev P;
+    float *feat;  // CL_IN per body
+};
+struct MlpArgs {
+    __half *par16;        // FP16 working parameters (CL_PARAMS)
+    float *par32;         // FP32 master parameters (training)
+    float *adam_m, *adam_v;
+    float *grad;          // CL_PARAMS
+    const float *x;       // n x CL_IN
+    const float *y;       // n x CL_OUT targets (training)
+    float *out;           // n x CL_OUT outputs (inference without apply)
+    float *loss;          // device scalar (may be null)
+    int n;
+};
+cudaError_t launch_closure_features(int prec, int next_odd, const ClosureArgs &a, cudaStream_t s);
+cudaError_t launch_mlp_infer(const MlpArgs &m, const ClosureArgs *apply, cudaStream_t s);
+cudaError_t launch_mlp_grad(const MlpArgs &m, cudaStream_t s);
+cudaError_t launch_adam(const MlpArgs &m, float lr, float beta1, float beta2, float eps, float c1, float c2,
+                        cudaStream_t s);
+cudaError_t launch_to_half(const float *src, __half *dst, int n, cudaStream_t s);
 int sweep_max_active_blocks(int prec, int variant, int block);
 constexpr int STAGED_TILE = 256;
 

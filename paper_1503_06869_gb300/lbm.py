@@ -81,6 +81,14 @@ SIGNATURES = {
     "lbm_get_sweep_timing": (C.c_int, [C.c_void_p, C.POINTER(C.c_double),
                                        C.POINTER(C.c_longlong)]),
     "lbm_get_launch_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong)]),
+    "lbm_set_closure": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "lbm_closure_features": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "lbm_mlp_create": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "lbm_mlp_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "lbm_mlp_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "lbm_mlp_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_float, C.c_void_p]),
+    "lbm_mlp_get_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "lbm_mlp_destroy": (C.c_int, [C.c_void_p]),
     "lbm_destroy": (C.c_int, [C.c_void_p]),
     "lbm_last_error": (C.c_char_p, [C.c_void_p]),
     "lbm_status_string": (C.c_char_p, [C.c_int]),
@@ -244,6 +252,60 @@ def lbm_get_launch_count(ctx) -> int:
 
 def lbm_destroy(ctx):
     _check(load().lbm_destroy(ctx))
+
+
+CLOSURE_IN, CLOSURE_OUT, CLOSURE_PARAMS = 86, 6, 14278
+
+
+def lbm_set_closure(ctx, params_fp16: Optional[np.ndarray]):
+    """Enable the learned closure with FP16 parameters (None disables)."""
+    if params_fp16 is None:
+        _check(load().lbm_set_closure(ctx, None, 0), ctx)
+        return
+    p = np.ascontiguousarray(params_fp16, dtype=np.float16)
+    _check(load().lbm_set_closure(ctx, _ptr(p), p.nbytes), ctx)
+
+
+def lbm_closure_features(ctx, n: int) -> np.ndarray:
+    out = np.zeros((n, CLOSURE_IN), dtype=np.float32)
+    _check(load().lbm_closure_features(ctx, _ptr(out), n), ctx)
+    return out
+
+
+def lbm_mlp_create(params: np.ndarray, stream_handle: int = 0) -> C.c_void_p:
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    h = C.c_void_p()
+    _check(load().lbm_mlp_create(_ptr(p), C.c_void_p(stream_handle), C.byref(h)))
+    return h
+
+
+def lbm_mlp_forward(m, x_ptr: int, y_ptr: int, n: int):
+    _check(load().lbm_mlp_forward(m, C.c_void_p(x_ptr), C.c_void_p(y_ptr), n))
+
+
+def lbm_mlp_grad(m, x_ptr: int, y_ptr: int, n: int, grad_ptr: int = 0) -> float:
+    loss = np.zeros(1, dtype=np.float32)
+    _check(load().lbm_mlp_grad(m, C.c_void_p(x_ptr), C.c_void_p(y_ptr), n, C.c_void_p(grad_ptr or None),
+                               _ptr(loss)))
+    return float(loss[0])
+
+
+def lbm_mlp_train_step(m, x_ptr: int, y_ptr: int, n: int, lr: float, want_loss: bool = True):
+    loss = np.zeros(1, dtype=np.float32)
+    _check(load().lbm_mlp_train_step(m, C.c_void_p(x_ptr), C.c_void_p(y_ptr), n, C.c_float(lr),
+                                     _ptr(loss) if want_loss else None))
+    return float(loss[0]) if want_loss else None
+
+
+def lbm_mlp_get_params(m):
+    p32 = np.zeros(CLOSURE_PARAMS, dtype=np.float32)
+    p16 = np.zeros(CLOSURE_PARAMS, dtype=np.float16)
+    _check(load().lbm_mlp_get_params(m, _ptr(p32), _ptr(p16)))
+    return p32, p16
+
+
+def lbm_mlp_destroy(m):
+    _check(load().lbm_mlp_destroy(m))
 
 
 # ---------------------------------------------------------------------------

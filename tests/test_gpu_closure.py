@@ -1,0 +1,227 @@
+"""GPU parity of the learned closure: features, FP16 tensor-core network
+(forward, gradient, Adam training) and its application in the time step,
+each against the FP64 closure oracle on the same seeded inputs.
+
+Tolerances: network outputs and gradients relative L2 2e-2 (FP16 operands
+and activations, FP32 accumulation, against FP64 with the same FP16-rounded
+parameters and inputs); features 1e-3 (FP32 interpolation at FP32 sample
+points); the applied correction 1e-6 relative (the same FP64 update fed the
+correction as an external load).
+"""
+import numpy as np
+import pytest
+
+from oracle import closure as cl
+from lbm_inputs import small_shear, shear_lattice, Particle, quat_from_axis
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1503_06869_gb300 import _build, lbm as L
+    _build.build()
+    L.load()
+    return L, torch
+
+
+def he_params(seed, scale=1.0):
+    rng = np.random.default_rng(seed)
+    layers = [(rng.normal(size=(o, i)) * scale * np.sqrt(2.0 / i), 0.1 * rng.normal(size=o)) for o, i in cl.LAYERS]
+    return cl.pack(layers)
+
+
+def f16(a):
+    return np.asarray(a, dtype=np.float16).astype(np.float64)
+
+
+def rel_l2(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300)
+
+
+def dev(torch, a):
+    return torch.tensor(np.ascontiguousarray(a, dtype=np.float32), device="cuda")
+
+
+@pytest.mark.parametrize("n", [1, 128, 300])
+def test_forward_matches_oracle(env, n):
+    L, torch = env
+    theta = he_params(1)
+    X = np.random.default_rng(2).normal(size=(n, cl.N_IN))
+    m = L.lbm_mlp_create(theta)
+    try:
+        x, y = dev(torch, X), torch.zeros((n, cl.N_OUT), device="cuda")
+        L.lbm_mlp_forward(m, x.data_ptr(), y.data_ptr(), n)
+        torch.cuda.synchronize()
+        want, _ = cl.forward(f16(theta), f16(X))
+        err = rel_l2(y.cpu().numpy(), want)
+        assert err < 2e-2, err
+    finally:
+        L.lbm_mlp_destroy(m)
+
+
+@pytest.mark.parametrize("n", [64, 300])
+def test_gradient_matches_oracle(env, n):
+    L, torch = env
+    theta = he_params(3)
+    rng = np.random.default_rng(4)
+    X, Y = rng.normal(size=(n, cl.N_IN)), rng.normal(size=(n, cl.N_OUT))
+    m = L.lbm_mlp_create(theta)
+    try:
+        x, y = dev(torch, X), dev(torch, Y)
+        g = torch.zeros(cl.N_PARAMS, device="cuda")
+        loss = L.lbm_mlp_grad(m, x.data_ptr(), y.data_ptr(), n, g.data_ptr())
+        want_loss, want_g = cl.loss_and_grad(f16(theta), f16(X), Y)
+        assert abs(loss - want_loss) <= 2e-2 * want_loss
+        got = g.cpu().numpy().astype(np.float64)
+        k = 0
+        for o, i in cl.LAYERS:   # every weight and bias block on its own
+            for a, b in ((k, k + o * i), (k + o * i, k + o * i + o)):
+                err = rel_l2(got[a:b], want_g[a:b])
+                assert err < 2e-2, (o, i, a, err)
+            k += o * i + o
+    finally:
+        L.lbm_mlp_destroy(m)
+
+
+def test_adam_training_tracks_the_oracle(env):
+    # student fits a teacher network of the same shape; GPU (FP16 operands,
+    # FP32 master parameters) and oracle (FP64) take the same Adam steps
+    L, torch = env
+    n, steps, lr = 256, 60, 2e-3
+    rng = np.random.default_rng(5)
+    X = rng.normal(size=(n, cl.N_IN))
+    Y, _ = cl.forward(he_params(6, 0.5), X)
+    theta0 = f16(he_params(7))
+    m = L.lbm_mlp_create(theta0)
+    try:
+        x, y = dev(torch, X), dev(torch, Y)
+        gpu = [L.lbm_mlp_train_step(m, x.data_ptr(), y.data_ptr(), n, lr) for _ in range(steps)]
+        final_gpu = L.lbm_mlp_grad(m, x.data_ptr(), y.data_ptr(), n)
+    finally:
+        L.lbm_mlp_destroy(m)
+    th, opt, ref = theta0.copy(), cl.Adam(cl.N_PARAMS), []
+    for _ in range(steps):
+        loss, g = cl.loss_and_grad(th, X, Y)
+        ref.append(loss)
+        th = opt.step(th, g, lr)
+    final_ref = cl.loss_and_grad(th, X, Y)[0]
+    assert abs(gpu[0] - ref[0]) <= 2e-2 * ref[0]
+    assert final_gpu < 0.5 * gpu[0]
+    assert 0.7 < final_gpu / final_ref < 1.4, (final_gpu, final_ref)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+def test_features_match_oracle(env, prec):
+    L, _ = env
+    w = small_shear(seed=3)
+    lat = w.lattices[0]
+    g = L.Simulation(w.lattices, w.particles, prec=prec)
+    try:
+        g.step(23)                      # odd count: the next sweep is odd
+        feats = L.lbm_closure_features(g.h, 1)
+        _, u, _, _, _ = g.fields(0, pdfs=False)
+        p = g.particles()[0]
+        gam = cl.wall_shear_rate(lat.ny, lat.wall_u_lo[0], lat.wall_u_hi[0])
+        want = cl.features(u, (lat.nx, lat.ny, lat.nz), lat.periodic, p[0:3], p[3:7], p[7:10], p[13:16], gam)
+        np.testing.assert_allclose(feats[0], want, rtol=1e-3, atol=1e-3)
+        g.step(1)                       # and after an even count
+        feats = L.lbm_closure_features(g.h, 1)
+        _, u, _, _, _ = g.fields(0, pdfs=False)
+        p = g.particles()[0]
+        want = cl.features(u, (lat.nx, lat.ny, lat.nz), lat.periodic, p[0:3], p[3:7], p[7:10], p[13:16], gam)
+        np.testing.assert_allclose(feats[0], want, rtol=1e-3, atol=1e-3)
+    finally:
+        g.close()
+
+
+def bias_only_params(b4):
+    layers = [(np.zeros((o, i)), np.zeros(o)) for o, i in cl.LAYERS]
+    layers[3][1][:] = b4
+    return cl.pack(layers)
+
+
+def test_closure_correction_enters_the_rigid_body_update(env):
+    # constant network output: the correction is R (o[:3] mu gam a b,
+    # o[3:] mu gam a^2 b); the same correction given as an external load
+    # must produce the same bodies after one step
+    L, _ = env
+    w = small_shear(seed=4)
+    lat, part = w.lattices[0], w.particles[0]
+    b4 = np.array([1.0, -0.5, 0.25, 2.0, 0.5, -1.0])
+    theta = bias_only_params(b4)
+    gam = cl.wall_shear_rate(lat.ny, lat.wall_u_lo[0], lat.wall_u_hi[0])
+    dF, dM = cl.closure_delta(theta, np.zeros(cl.N_IN), part.quat, part.semi_axes, lat.tau, lat.rho0, gam)
+    a = L.Simulation(w.lattices, w.particles, prec="f64")
+    b = L.Simulation(w.lattices, w.particles, prec="f64")
+    try:
+        L.lbm_set_closure(a.h, theta.astype(np.float16))
+        L.lbm_set_external(b.h, dF[None, :].copy(), dM[None, :].copy(), 1)
+        a.step(1)
+        b.step(1)
+        pa, pb = a.particles()[0], b.particles()[0]
+        scale_v = np.abs(dF).max() / (part.density * 4 / 3 * np.pi * np.prod(part.semi_axes))
+        assert np.abs(pa[7:10] - pb[7:10]).max() <= 1e-6 * scale_v
+        assert np.abs(pa[10:13] - pb[10:13]).max() <= 1e-6 * np.abs(pb[10:13]).max() + 1e-18
+        Fa, Ma = a.forces()
+        Fb, Mb = b.forces()
+        np.testing.assert_allclose(Fa[0] - Fb[0], dF, rtol=1e-6, atol=1e-6 * np.abs(dF).max())
+        np.testing.assert_allclose(Ma[0] - Mb[0], dM, rtol=1e-6, atol=1e-6 * np.abs(dM).max())
+    finally:
+        a.close()
+        b.close()
+
+
+def test_closure_graph_replay_matches_eager(env):
+    L, _ = env
+    w = small_shear(seed=6)
+    theta = f16(he_params(8, 0.05))
+    a = L.Simulation(w.lattices, w.particles, prec="f32")
+    b = L.Simulation(w.lattices, w.particles, prec="f32")
+    try:
+        L.lbm_set_graphs(b.h, False)
+        for s in (a, b):
+            L.lbm_set_closure(s.h, theta.astype(np.float16))
+            s.step(9)
+        pa, pb = a.particles(), b.particles()
+        np.testing.assert_allclose(pa[:, :13], pb[:, :13], rtol=1e-9, atol=1e-12)
+    finally:
+        a.close()
+        b.close()
+
+
+def test_zero_closure_changes_nothing(env):
+    L, _ = env
+    w = small_shear(seed=5)
+    a = L.Simulation(w.lattices, w.particles, prec="f32")
+    b = L.Simulation(w.lattices, w.particles, prec="f32")
+    try:
+        L.lbm_set_closure(a.h, np.zeros(cl.N_PARAMS, dtype=np.float16))
+        a.step(20)
+        b.step(20)
+        np.testing.assert_allclose(a.particles(), b.particles(), rtol=0, atol=1e-12)
+    finally:
+        a.close()
+        b.close()
+
+
+def test_closure_is_off_without_moving_walls(env):
+    # a fully periodic lattice has no shear rate: no correction
+    L, _ = env
+    from lbm_inputs import Lattice
+    lat = Lattice(32, 32, 32, tau=0.8, periodic=(1, 1, 1))
+    p = Particle(pos=(15.5, 15.5, 15.5), quat=quat_from_axis((1.0, 0.0, 0.0)), semi_axes=(6.0, 2.0, 2.0),
+                 vel=(0.01, 0.0, 0.0))
+    a = L.Simulation([lat], [p], prec="f32")
+    b = L.Simulation([lat], [p], prec="f32")
+    try:
+        L.lbm_set_closure(a.h, bias_only_params(np.ones(6)).astype(np.float16))
+        a.step(4)
+        b.step(4)
+        np.testing.assert_allclose(a.particles(), b.particles(), rtol=0, atol=1e-12)
+    finally:
+        a.close()
+        b.close()
