@@ -29,7 +29,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from lbm_inputs import large_shear, small_shear, batched_shear  # noqa: E402
+from lbm_inputs import large_shear, small_shear, batched_shear, fibre_suspension  # noqa: E402
 
 BYTES_PER_POP = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
 
@@ -68,6 +68,8 @@ def workload(name: str):
         return small_shear(seed=1)
     if name == "batched":
         return batched_shear(seed=1)
+    if name == "fibre":
+        return fibre_suspension(seed=1)
     raise ValueError(name)
 
 
@@ -207,7 +209,8 @@ def config_of(w, args, nfluid):
     cfg = {"workload": w.name, "lattices": len(w.lattices),
            "cells": int(w.ncells), "particles": len(w.particles), "precision": args.prec,
            "l2": "inputs larger than L2 (populations %.0f MB)" % (w.ncells * 19 * BYTES_PER_POP[args.prec] / 1e6),
-           "parallelism": f"replica x{args.gpus}"}
+           "parallelism": f"replica x{args.gpus}",
+           "closure": bool(getattr(args, "closure", False))}
     if len(w.lattices) == 1:
         cfg["lattice"] = [lat.nx, lat.ny, lat.nz]
         cfg["tau"] = lat.tau
@@ -222,7 +225,9 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="large", choices=["large", "small", "batched"])
+    ap.add_argument("--workload", default="large", choices=["large", "small", "batched", "fibre"])
+    ap.add_argument("--closure", action="store_true",
+                    help="enable the learned force/torque closure (seeded small parameters)")
     ap.add_argument("--prec", default="f32", choices=["f64", "f32", "f16", "bf16"])
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -237,6 +242,10 @@ def main():
     torch.cuda.set_device(local)
     sim = lbm.Simulation(w.lattices, w.particles, prec=args.prec, device=local)
     h = sim.h
+    if args.closure:
+        # throughput only: the parameters are seeded and small, not trained
+        theta = np.random.default_rng(0).normal(size=lbm.CLOSURE_PARAMS) * 0.01
+        lbm.lbm_set_closure(h, theta.astype(np.float16))
     lbm.lbm_autotune(h)
     info = lbm.lbm_get_info(h)
     sim.step(args.warmup)

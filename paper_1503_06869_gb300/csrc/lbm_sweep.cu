@@ -202,39 +202,27 @@ __device__ __forceinline__ void tacc_add(const SweepArgs &a, uint32_t *tkey, typ
 // Momentum handed over by the links of one cell to one body or wall
 // (Eq. TransferredMomentum): the link momentum (2 f~_q - 6 w_q rho0 c_q.u_s) c_q
 // is split into the small part (2 g~_q - 6 w_q rho0 c_q.u_s) c_q, g~ the stored
-// post-collision offset, summed with compensation in the compute precision,
-// and the constant part 2 w_q rho0 c_q = (rho0/18) (36 w_q) c_q, counted
-// exactly as the integer vector sum of (36 w_q) c_q.
-template <class C> struct LinkSum {
-    C s[3] = {0, 0, 0}, e[3] = {0, 0, 0};
-    int n[3] = {0, 0, 0};
-    __device__ __forceinline__ void add(int k, C v) {
-        if constexpr (sizeof(C) == 4) {
-            const df t = two_sum(s[k], v);
-            s[k] = t.hi;
-            e[k] = __fadd_rn(e[k], t.lo);
-        } else {
-            s[k] += v;
-        }
-    }
-    // link q (an unrolled loop index, so the branches fold) with small part sm
-    __device__ __forceinline__ void link(int q, C sm) {
-        const int w36 = q <= 6 ? 2 : 1;
-        if (cx(q)) { add(0, cx(q) > 0 ? sm : -sm); n[0] += cx(q) * w36; }
-        if (cy(q)) { add(1, cy(q) > 0 ? sm : -sm); n[1] += cy(q) * w36; }
-        if (cz(q)) { add(2, cz(q) > 0 ? sm : -sm); n[2] += cz(q) * w36; }
-    }
-};
-
-// Total momentum of a LinkSum: F_k = small_k + (rho0/18) n_k.
+// post-collision offset (of the order of the deviation from rest), summed in
+// the compute precision over the cell's at most 18 links, and the constant
+// part 2 w_q rho0 c_q = (rho0/18) (36 w_q) c_q, whose sum over the links in
+// `mask` is rho0/18 times an exact integer vector.  F = small + constant.
 template <int PREC, class C>
-__device__ __forceinline__ void link_force(const LatDev &L, const LinkSum<C> &ls, typename Acc<PREC>::V F[3]) {
+__device__ __forceinline__ void link_force(const LatDev &L, const C (&small)[3], uint32_t mask,
+                                           typename Acc<PREC>::V F[3]) {
+    int n[3] = {0, 0, 0};
+#pragma unroll
+    for (int q = 1; q < Q; ++q)
+        if ((mask >> q) & 1u) {
+            const int w36 = q <= 6 ? 2 : 1;
+            n[0] += cx(q) * w36;
+            n[1] += cy(q) * w36;
+            n[2] += cz(q) * w36;
+        }
     if constexpr (PREC == LBM_F64) {
-        for (int k = 0; k < 3; ++k) F[k] = ls.s[k] + L.rho18 * (double)ls.n[k];
+        for (int k = 0; k < 3; ++k) F[k] = small[k] + L.rho18 * (double)n[k];
     } else {
         const df r18 = {L.rho18f[0], L.rho18f[1]};
-        for (int k = 0; k < 3; ++k)
-            F[k] = df_add(two_sum(ls.s[k], ls.e[k]), df_mul_f(r18, (float)ls.n[k]));
+        for (int k = 0; k < 3; ++k) F[k] = df_add_f(df_mul_f(r18, (float)n[k]), small[k]);
     }
 }
 
@@ -331,6 +319,34 @@ __device__ __noinline__ double bounce_link(const SweepArgs &a, const LatDev &L, 
     return ft - dbb;
 }
 
+// Links of a near-obstacle cell to bodies other than the first one met and to
+// a second moving wall layer (rare): the sweep has stored the unbounced
+// post-collision value in the bounce-back slot opp(q) of x; bounce_link turns
+// it into the reflected value and books the momentum.  Kept out of the link
+// loop, so that the loop makes no calls.
+template <int PREC>
+__device__ __noinline__ void other_links(const SweepArgs &a, const LatDev &L, int li, int idx, uint32_t mask,
+                                         uint32_t *tkey, typename Acc<PREC>::V *tval) {
+    using S = Store<PREC>;
+    using T = typename S::T;
+    T *base = reinterpret_cast<T *>(a.f) + L.f_off;
+    const long long np = L.npad;
+    const CellGeom cg = cell_geom(L, idx);
+    for (uint32_t m = mask; m; m &= m - 1) {
+        const int q = __ffs(m) - 1;
+        const int qx = c_cx[q], qy = c_cy[q], qz = c_cz[q];
+        const int qo = q == 0 ? 0 : ((q & 1) ? q + 1 : q - 1);
+        int nb = 0;
+        nb += qx < 0 ? cg.dxm : (qx > 0 ? cg.dxp : 0);
+        nb += qy < 0 ? cg.dym : (qy > 0 ? cg.dyp : 0);
+        nb += qz < 0 ? cg.dzm : (qz > 0 ? cg.dzp : 0);
+        T *slot = base + qo * np + idx;
+        const double v = bounce_link<PREC>(a, L, li, q, idx + nb, wrapc(cg.x + qx, L.nx), wrapc(cg.y + qy, L.ny),
+                                           wrapc(cg.z + qz, L.nz), (double)S::ld(slot), tkey, tval);
+        S::st(slot, (typename S::C)v);
+    }
+}
+
 // Fluid cell next to walls or obstacles: neighbour flags decide where each
 // population is read from (odd steps) and which outgoing populations are
 // bounced back.
@@ -379,14 +395,15 @@ __device__ __forceinline__ typename Store<PREC>::C ring_value(const typename Rin
 }
 
 // Population source of the near-obstacle path: VIEW 0 reads global memory,
-// 1 the bulk-copy stage window `src`, 2 the thread's ring column `src`; the
-// populations bounced off obstacles in the previous step always come from
-// global memory.
-// Only scalars and pointers cross the call, so the caller's register arrays
-// never need an address (which would put them in local memory on every path).
+// 1 the bulk-copy stage window `src`, 2 the thread's ring column `src`, 3
+// finds the bulk pull values in g already (the direct sweep loads them with
+// the flag byte); the populations bounced off obstacles in the previous step
+// always come from global memory.  Inlined: the caller's arrays stay in
+// registers.
 template <int PREC, int ODD, int VIEW>
-__device__ __noinline__ void near_cell(const SweepArgs &a, const LatDev &L, int li, int idx,
-                                       uint32_t *tkey, typename Acc<PREC>::V *tval, const void *src) {
+__device__ __forceinline__ void near_cell(const SweepArgs &a, const LatDev &L, int li, int idx,
+                                          uint32_t *tkey, typename Acc<PREC>::V *tval, const void *src,
+                                          typename Store<PREC>::C (&g)[Q]) {
     using S = Store<PREC>;
     using T = typename S::T;
     using C = typename S::C;
@@ -404,50 +421,27 @@ __device__ __noinline__ void near_cell(const SweepArgs &a, const LatDev &L, int 
         if (f & F_SOLID) solid |= 1u << q;
         if (f & F_WALL) wall |= 1u << q;
     }
-    C g[Q];
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        const int p = opp(q);
-        if (!ODD) {
-            if (VIEW == 1) g[q] = S::ld(stage + q * Cfg::W + threadIdx.x);
-            else if (VIEW == 2) g[q] = ring_value<PREC>(col, q, idx & 1);
-            else if (VIEW == 3) g[q] = reinterpret_cast<const C *>(src)[q];
-            else g[q] = S::ld(base + q * np + idx);
-        } else if ((solid >> p) & 1u) {
-            g[q] = S::ld(base + q * np + idx);
-        } else if (VIEW == 3) {
-            g[q] = reinterpret_cast<const C *>(src)[q];
-        } else if (VIEW == 1) {
-            g[q] = S::ld(stage + q * Cfg::W + (L.off[p] & (Cfg::A - 1)) + threadIdx.x);
-        } else if (VIEW == 2) {
-            g[q] = ring_value<PREC>(col, q, (idx + nb_off(cg, p)) & 1);
-        } else {
-            g[q] = S::ld(base + p * np + idx + nb_off(cg, p));
-        }
-    }
-    // Obstacle links: the ids of all obstacle neighbours are requested in one
-    // round trip; the first body met (p0) has its motion loaded once and its
-    // links are bounced inline in the compute precision, their momentum
-    // gathered in a LinkSum; links to any further body take bounce_link.
+    // Obstacle links: the first body met (p0) has its motion loaded once and
+    // its links are bounced inline in the compute precision, their momentum
+    // summed per cell; links to any further body take bounce_link.  The
+    // ids and the body's motion are settled before the populations are
+    // loaded, so that only the populations and the sums stay live through
+    // the link loop (the path runs under the sweep's register budget).
     const uint32_t obst = solid & ~wall;
     uint32_t p0 = SLOT_EMPTY, m0 = 0;
-    if (obst) {
-        uint32_t ids[Q];
 #pragma unroll
-        for (int q = 1; q < Q; ++q)
-            ids[q] = ((obst >> q) & 1u) ? a.pid[L.c_off + idx + nb_off(cg, q)] : SLOT_EMPTY;
-#pragma unroll
-        for (int q = 1; q < Q; ++q)
-            if (ids[q] != SLOT_EMPTY) {
-                if (p0 == SLOT_EMPTY) p0 = ids[q];
-                if (ids[q] == p0) m0 |= 1u << q;
-            }
-    }
-    // body p0: lever arm r_F of this cell, velocity U and angular velocity W
+    for (int q = 1; q < Q; ++q)
+        if ((obst >> q) & 1u) {
+            const uint32_t id = a.pid[L.c_off + idx + nb_off(cg, q)];
+            if (p0 == SLOT_EMPTY) p0 = id;
+            if (id == p0) m0 |= 1u << q;
+        }
+    // body p0: lever arm r_F of this cell (compute precision), velocity U and
+    // angular velocity W
     using A = Acc<PREC>;
-    typename A::V rF[3];
     C rc[3] = {0, 0, 0}, bU[3] = {0, 0, 0}, bW[3] = {0, 0, 0};
     if (p0 != SLOT_EMPTY) {
+        typename A::V rF[3];
         lever_arm<PREC>(a, L, p0, cg.x, cg.y, cg.z, rF);
         for (int k = 0; k < 3; ++k) {
             if constexpr (PREC == LBM_F64) {
@@ -461,43 +455,68 @@ __device__ __noinline__ void near_cell(const SweepArgs &a, const LatDev &L, int 
             }
         }
     }
+    if (VIEW == 3) {
+        if (ODD) {
+#pragma unroll
+            for (int q = 0; q < Q; ++q)
+                if ((solid >> opp(q)) & 1u) g[q] = S::ld(base + q * np + idx);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int p = opp(q);
+            if (!ODD) {
+                if (VIEW == 1) g[q] = S::ld(stage + q * Cfg::W + threadIdx.x);
+                else if (VIEW == 2) g[q] = ring_value<PREC>(col, q, idx & 1);
+                else g[q] = S::ld(base + q * np + idx);
+            } else if ((solid >> p) & 1u) {
+                g[q] = S::ld(base + q * np + idx);
+            } else if (VIEW == 1) {
+                g[q] = S::ld(stage + q * Cfg::W + (L.off[p] & (Cfg::A - 1)) + threadIdx.x);
+            } else if (VIEW == 2) {
+                g[q] = ring_value<PREC>(col, q, (idx + nb_off(cg, p)) & 1);
+            } else {
+                g[q] = S::ld(base + p * np + idx + nb_off(cg, p));
+            }
+        }
+    }
     collide_lat<C>(g, L);
-    // Wall links are bounced inline as well: the wall layer that is hit
-    // follows from the neighbour's y (a y = 0 or y = ny-1 layer of a
-    // non-periodic y axis moves, any other wall layer rests).
-    LinkSum<C> lw, lb;
-    int wside = -1;
+    // Wall links are bounced inline as well.  The y = 0 and y = ny-1 layers of
+    // a non-periodic y axis move; their links (wmain: the layer met first)
+    // hand momentum to that wall; any other wall layer rests.  A cell touching
+    // both moving layers (ny = 3) sends the second layer's links through
+    // bounce_link.
+    uint32_t wlo = 0, whi = 0;
+    if (wall && !L.py) {
+#pragma unroll
+        for (int q = 1; q < Q; ++q)
+            if ((wall >> q) & 1u) {
+                if (cg.y + cy(q) == 0) wlo |= 1u << q;
+                else if (cg.y + cy(q) == L.ny - 1) whi |= 1u << q;
+            }
+    }
+    const int wside = wlo ? 0 : (whi ? 1 : -1);
+    const uint32_t wmain = wlo ? wlo : whi;
+    const uint32_t wrest = wall & ~(wlo | whi);
     const LatPar<C> lp(L);
     const C rho0c = lp.rho0;
+    const C *uw = wside == 1 ? lp.whi : lp.wlo;
+    C sw[3] = {0, 0, 0}, sb[3] = {0, 0, 0};  // small parts of the wall / body p0 momentum
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-        if ((wall >> q) & 1u) {
-            const int ys = cg.y + cy(q);
-            int side = -1;
-            C u0 = 0, u1 = 0, u2 = 0;
-            if (!L.py && ys == 0) {
-                side = 0;
-                u0 = lp.wlo[0]; u1 = lp.wlo[1]; u2 = lp.wlo[2];
-            } else if (!L.py && ys == L.ny - 1) {
-                side = 1;
-                u0 = lp.whi[0]; u1 = lp.whi[1]; u2 = lp.whi[2];
-            }
+        if ((wmain >> q) & 1u) {
             C cu = 0;
-            if (cx(q)) cu += cx(q) > 0 ? u0 : -u0;
-            if (cy(q)) cu += cy(q) > 0 ? u1 : -u1;
-            if (cz(q)) cu += cz(q) > 0 ? u2 : -u2;
+            if (cx(q)) cu += cx(q) > 0 ? uw[0] : -uw[0];
+            if (cy(q)) cu += cy(q) > 0 ? uw[1] : -uw[1];
+            if (cz(q)) cu += cz(q) > 0 ? uw[2] : -uw[2];
             const C dbb = C(6.0 * wq(q)) * rho0c * cu;
-            if (side >= 0) {
-                if (wside >= 0 && side != wside) {  // a cell touching both y walls (ny = 3): hand over first
-                    typename A::V F[3];
-                    link_force<PREC>(L, lw, F);
-                    tacc_add<PREC>(a, tkey, tval, KEY_WALL | ((uint32_t)li << 1) | (uint32_t)wside, F, 3);
-                    lw = LinkSum<C>();
-                }
-                wside = side;
-                lw.link(q, C(2) * g[q] - dbb);
-            }
+            const C sm = C(2) * g[q] - dbb;
+            if (cx(q)) sw[0] += cx(q) > 0 ? sm : -sm;
+            if (cy(q)) sw[1] += cy(q) > 0 ? sm : -sm;
+            if (cz(q)) sw[2] += cz(q) > 0 ? sm : -sm;
             S::st(base + opp(q) * np + idx, g[q] - dbb);
+        } else if ((wrest >> q) & 1u) {
+            S::st(base + opp(q) * np + idx, g[q]);
         } else if ((m0 >> q) & 1u) {
             // velocity bounce-back off body p0 (Eq. LBMMovWall): u_s at the
             // obstacle cell x_F + c_q, lever arm r_F + c_q
@@ -510,27 +529,32 @@ __device__ __noinline__ void near_cell(const SweepArgs &a, const LatDev &L, int 
             if (cy(q)) cu += cy(q) > 0 ? us1 : -us1;
             if (cz(q)) cu += cz(q) > 0 ? us2 : -us2;
             const C dbb = C(6.0 * wq(q)) * rho0c * cu;
+            const C sm = C(2) * g[q] - dbb;
+            if (cx(q)) sb[0] += cx(q) > 0 ? sm : -sm;
+            if (cy(q)) sb[1] += cy(q) > 0 ? sm : -sm;
+            if (cz(q)) sb[2] += cz(q) > 0 ? sm : -sm;
             S::st(base + opp(q) * np + idx, g[q] - dbb);
-            lb.link(q, C(2) * g[q] - dbb);
         } else if ((solid >> q) & 1u) {
-            const double v = bounce_link<PREC>(a, L, li, q, idx + nb_off(cg, q), wrapc(cg.x + cx(q), L.nx),
-                                               wrapc(cg.y + cy(q), L.ny), wrapc(cg.z + cz(q), L.nz),
-                                               (double)g[q], tkey, tval);
-            S::st(base + opp(q) * np + idx, (C)v);
+            // another body (or the second moving wall layer): the unbounced
+            // value goes to the bounce-back slot now, other_links rewrites it
+            S::st(base + opp(q) * np + idx, g[q]);
         } else if (!ODD) {
             S::st(base + opp(q) * np + idx, g[q]);
         } else {
             S::st(base + q * np + idx + nb_off(cg, q), g[q]);
         }
     }
-    if (p0 != SLOT_EMPTY) {
-        typename A::V F[3];
-        link_force<PREC>(L, lb, F);
+    const uint32_t mo = solid & ~(m0 | wmain | wrest);
+    if (mo) other_links<PREC>(a, L, li, idx, mo, tkey, tval);
+    if (m0) {
+        typename A::V F[3], rF[3];
+        link_force<PREC>(L, sb, m0, F);
+        lever_arm<PREC>(a, L, p0, cg.x, cg.y, cg.z, rF);
         body_add<PREC>(a, tkey, tval, p0, F, rF);
     }
-    if (wside >= 0) {
+    if (wmain) {
         typename A::V F[3];
-        link_force<PREC>(L, lw, F);
+        link_force<PREC>(L, sw, wmain, F);
         tacc_add<PREC>(a, tkey, tval, KEY_WALL | ((uint32_t)li << 1) | (uint32_t)wside, F, 3);
     }
 }
@@ -565,7 +589,8 @@ __device__ __noinline__ void wall_cell(const SweepArgs &a, const LatDev &L, int 
     const LatPar<C> lp(L);
     const C *uw = SIDE == 0 ? lp.wlo : lp.whi;
     const C u0 = uw[0], u1 = uw[1], u2 = uw[2], rho0c = lp.rho0;
-    LinkSum<C> lw;
+    C sw[3] = {0, 0, 0};
+    uint32_t mask = 0;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         if (SIDE == 0 ? cy(q) < 0 : cy(q) > 0) {
@@ -575,7 +600,11 @@ __device__ __noinline__ void wall_cell(const SweepArgs &a, const LatDev &L, int 
             if (cz(q)) cu += cz(q) > 0 ? u2 : -u2;
             const C dbb = C(6.0 * wq(q)) * rho0c * cu;
             S::st(base + opp(q) * np + idx, g[q] - dbb);
-            lw.link(q, C(2) * g[q] - dbb);
+            const C sm = C(2) * g[q] - dbb;
+            if (cx(q)) sw[0] += cx(q) > 0 ? sm : -sm;
+            sw[1] += cy(q) > 0 ? sm : -sm;
+            if (cz(q)) sw[2] += cz(q) > 0 ? sm : -sm;
+            mask |= 1u << q;
         } else if (!ODD) {
             S::st(base + opp(q) * np + idx, g[q]);
         } else {
@@ -583,7 +612,7 @@ __device__ __noinline__ void wall_cell(const SweepArgs &a, const LatDev &L, int 
         }
     }
     typename Acc<PREC>::V F[3];
-    link_force<PREC>(L, lw, F);
+    link_force<PREC>(L, sw, mask, F);
     tacc_add<PREC>(a, tkey, tval, KEY_WALL | ((uint32_t)li << 1) | (uint32_t)SIDE, F, 3);
 }
 
@@ -700,8 +729,8 @@ __global__ void __launch_bounds__(256, SweepBounds<PREC>::MINB)
                 wall_cell<PREC, ODD, 1>(a, L, li, idx, &tkey[threadIdx.x], tval[threadIdx.x]);
             continue;
         }
-        if (fl & F_NEAR) {  // reload from global memory inside the near path
-            near_cell<PREC, ODD, 0>(a, L, li, idx, &tkey[threadIdx.x], tval[threadIdx.x], nullptr);
+        if (fl & F_NEAR) {
+            near_cell<PREC, ODD, 3>(a, L, li, idx, &tkey[threadIdx.x], tval[threadIdx.x], nullptr, g);
             continue;
         }
         collide_lat<C>(g, L);
@@ -899,10 +928,11 @@ __global__ void __launch_bounds__(256, SweepBounds<PREC>::MINB)
                         cg.dzm = cg.z == 0 ? (L.nz - 1) * sz : -sz;
                         cg.dzp = cg.z == L.nz - 1 ? -(L.nz - 1) * sz : sz;
                         if (fl & F_NEAR) {
+                            typename S::C g[Q];
                             if (interior)
-                                near_cell<PREC, ODD, 1>(a, L, li, idx, &tkey[tid], tval[tid], stage);
+                                near_cell<PREC, ODD, 1>(a, L, li, idx, &tkey[tid], tval[tid], stage, g);
                             else
-                                near_cell<PREC, ODD, 0>(a, L, li, idx, &tkey[tid], tval[tid], nullptr);
+                                near_cell<PREC, ODD, 0>(a, L, li, idx, &tkey[tid], tval[tid], nullptr, g);
                         } else {
                             bulk_cell<PREC, ODD>(a, L, idx);
                         }
@@ -1031,7 +1061,8 @@ __global__ void __launch_bounds__(256, SweepBounds<PREC>::MINB)
         if (fl & F_SOLID) continue;
         const CellGeom cg = cell_geom(L, idx);
         if (fl & F_NEAR) {
-            near_cell<PREC, ODD, 2>(a, L, li, idx, &tkey[tid], tval[tid], col);
+            C gn[Q];
+            near_cell<PREC, ODD, 2>(a, L, li, idx, &tkey[tid], tval[tid], col, gn);
             continue;
         }
         C g[Q];
