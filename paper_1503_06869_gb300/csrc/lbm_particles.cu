@@ -45,22 +45,6 @@ __device__ __forceinline__ double min_image_rn(double d, int n, int periodic) {
     return d;
 }
 
-// Rotation matrix of a unit quaternion (w,x,y,z), every operation rounded
-// separately in a fixed order so that the obstacle mapping is reproducible
-// bit for bit.
-__device__ __forceinline__ void quat_matrix_rn(const double *q, double R[9]) {
-    const double w = q[0], x = q[1], y = q[2], z = q[3];
-    R[0] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(__dmul_rn(y, y), __dmul_rn(z, z))));
-    R[1] = __dmul_rn(2.0, __dsub_rn(__dmul_rn(x, y), __dmul_rn(w, z)));
-    R[2] = __dmul_rn(2.0, __dadd_rn(__dmul_rn(x, z), __dmul_rn(w, y)));
-    R[3] = __dmul_rn(2.0, __dadd_rn(__dmul_rn(x, y), __dmul_rn(w, z)));
-    R[4] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(__dmul_rn(x, x), __dmul_rn(z, z))));
-    R[5] = __dmul_rn(2.0, __dsub_rn(__dmul_rn(y, z), __dmul_rn(w, x)));
-    R[6] = __dmul_rn(2.0, __dsub_rn(__dmul_rn(x, z), __dmul_rn(w, y)));
-    R[7] = __dmul_rn(2.0, __dadd_rn(__dmul_rn(y, z), __dmul_rn(w, x)));
-    R[8] = __dsub_rn(1.0, __dmul_rn(2.0, __dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y))));
-}
-
 // Cell centre (i,j,k) inside the ellipsoid: (p0/a)^2 + (p1/b)^2 + (p2/c)^2 <= 1
 // with p = R^T d and d the nearest-image displacement from the centre.
 __device__ __forceinline__ bool inside_rn(const LatDev &L, const double *pos, const double R[9],
@@ -136,17 +120,6 @@ __device__ __forceinline__ bool inside_fast(const LatDev &L, const double *pos, 
     return inside_rn(L, pos, R64, semi, i, j, k);
 }
 
-// Half extents of the world-aligned bounding box of a rotated ellipsoid, in
-// FP32 (the box only has to contain the body; the re-mapping region adds a
-// margin of two cells around it).
-__device__ __forceinline__ void aabb_half(const double R[9], const double *semi, float h[3]) {
-    for (int a = 0; a < 3; ++a) {
-        const float e0 = (float)R[3 * a + 0] * (float)semi[0], e1 = (float)R[3 * a + 1] * (float)semi[1],
-                    e2 = (float)R[3 * a + 2] * (float)semi[2];
-        h[a] = sqrtf(e0 * e0 + e1 * e1 + e2 * e2) * 1.0001f;
-    }
-}
-
 // ---------------------------------------------------------------------------
 // rigid-body update (one thread per body) and wall-force hand-over
 // ---------------------------------------------------------------------------
@@ -156,14 +129,47 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+__device__ __forceinline__ double sel3(int k, double v0, double v1, double v2) {
+    return k == 0 ? v0 : (k == 1 ? v1 : v2);
+}
+
+// Entry e = 3i + j (row-major) of the rotation matrix of the unit quaternion
+// (w, x, y, z) with v = (x, y, z), every product and sum rounded separately in
+// a fixed order (the host builds the initial matrix in the same order, so the
+// obstacle mapping is reproducible bit for bit): diagonal
+// 1 - 2(v_a v_a + v_b v_b) over the two other axes a < b, off-diagonal
+// 2(v_i v_j - eps_ijm w v_m).  Operands are selected, not branched on, so the
+// nine lanes of a warp evaluate one instruction stream.
+__device__ __forceinline__ double quat_entry_rn(int e, double w, double x, double y, double z) {
+    const int i = e / 3, j = e - 3 * (e / 3);
+    double pa, pb, pc, pd;
+    if (i == j) {
+        const int o1 = i == 0 ? 1 : 0, o2 = i == 2 ? 1 : 2;
+        pa = pb = sel3(o1, x, y, z);
+        pc = pd = sel3(o2, x, y, z);
+    } else {
+        const int m = 3 - i - j;
+        const bool cyclic = j - i == 1 || j - i == -2;  // eps_ijm = +1
+        pa = sel3(i, x, y, z);
+        pb = sel3(j, x, y, z);
+        pc = cyclic ? -w : w;
+        pd = sel3(m, x, y, z);
+    }
+    const double X = __dadd_rn(__dmul_rn(pa, pb), __dmul_rn(pc, pd));
+    const double t2 = __dmul_rn(2.0, X);
+    return i == j ? __dsub_rn(1.0, t2) : t2;
+}
+
 // One warp per body (and per lattice for the wall loads): lane c reads and
-// clears accumulator copy c, the warp sums the copies, and lane 0 runs the
-// body's update (Sec. 4.3) on register copies of its state: every load is
-// issued up front, every store at the end, so the FP64 chain pays one memory
-// round trip instead of one per dependent access.
+// clears accumulator copy c and the warp sums the copies; then the body's
+// update (Sec. 4.3) runs across the lanes -- lane k < 3 owns component k of
+// every vector, lane e < 9 entry e of the rotation -- so that the FP64 work,
+// which GB300 issues at a low rate per warp instruction, takes few
+// instructions.  Every load is issued up front, every store at the end.
 __global__ void rigid_body_kernel(RemapArgs a) {
     pdl_enter();
     static_assert(ACC_COPIES == 32, "one lane per accumulator copy");
+    const unsigned full = 0xffffffffu;
     const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     const PartDev &P = a.P;
@@ -180,66 +186,60 @@ __global__ void rigid_body_kernel(RemapArgs a) {
             for (int k = 0; k < 6; ++k) a.wall_last[6 * t + k] = s[k];
         return;
     }
-    const int t = warp;
-    double hs[6];  // F_h, M_h: the sweep's copies, summed
-    {
-        double *acc = P.acc + 6 * ((size_t)t * ACC_COPIES + lane);
-        for (int k = 0; k < 6; ++k) hs[k] = acc[k];
-        for (int k = 0; k < 6; ++k) acc[k] = 0.0;
-        for (int k = 0; k < 6; ++k) hs[k] = warp_sum(hs[k]);
-    }
-    if (lane != 0) return;
-
-    double pos[3], vel[3], om[3], Lm[3], q[4], semi[3], Iinv[3], eF[3], eM[3];
-    for (int k = 0; k < 3; ++k) {
-        pos[k] = P.pos[3 * t + k];
-        vel[k] = P.vel[3 * t + k];
-        om[k] = P.om[3 * t + k];
-        Lm[k] = P.L[3 * t + k];
-        semi[k] = P.semi[3 * t + k];
-        Iinv[k] = P.Iinv[3 * t + k];
-        eF[k] = P.extF[3 * t + k];
-        eM[k] = P.extM[3 * t + k];
-    }
-    for (int k = 0; k < 4; ++k) q[k] = P.quat[4 * t + k];
-    double Rold[9];  // rotation of q, stored by the previous update
-    for (int k = 0; k < 9; ++k) Rold[k] = P.R64[9 * (size_t)t + k];
+    const size_t t = (size_t)warp;
+    const int k = lane < 3 ? lane : 0;  // vector component of this lane (lanes >= 3 mirror 0, store nothing)
+    const bool vec = lane < 3;
+    // ---- loads
+    const double pos = P.pos[3 * t + k], vel = P.vel[3 * t + k], om = P.om[3 * t + k], Lm = P.L[3 * t + k];
+    const double Iinv = P.Iinv[3 * t + k], eF = P.extF[3 * t + k], eM = P.extM[3 * t + k];
+    const double s0 = P.semi[3 * t], s1 = P.semi[3 * t + 1], s2 = P.semi[3 * t + 2];
+    const double w = P.quat[4 * t], x = P.quat[4 * t + 1], y = P.quat[4 * t + 2], z = P.quat[4 * t + 3];
+    const double *Rp = P.R64 + 9 * t;  // rotation of q, stored by the previous update
+    const double Rr0 = Rp[3 * k], Rr1 = Rp[3 * k + 1], Rr2 = Rp[3 * k + 2];  // row k
+    const double Rc0 = Rp[k], Rc1 = Rp[3 + k], Rc2 = Rp[6 + k];              // column k
     const double minv = P.minv[t];
     const int fixed = P.fixed[t];
     const LatDev &Lt = a.lat[P.cell[t]];
-    const int dims[3] = {Lt.nx, Lt.ny, Lt.nz}, per[3] = {Lt.px, Lt.py, Lt.pz};
-
-    for (int k = 0; k < 6; ++k) P.last[6 * t + k] = hs[k];
-    for (int k = 0; k < 3; ++k) {
-        P.pos_old[3 * t + k] = pos[k];
-        P.vel_old[3 * t + k] = vel[k];
-        P.om_old[3 * t + k] = om[k];
+    const int dim = k == 0 ? Lt.nx : (k == 1 ? Lt.ny : Lt.nz);
+    const int per = k == 0 ? Lt.px : (k == 1 ? Lt.py : Lt.pz);
+    double hs[6];  // F_h, M_h: the sweep's copies, summed
+    {
+        double *acc = P.acc + 6 * (t * ACC_COPIES + lane);
+        for (int c = 0; c < 6; ++c) hs[c] = acc[c];
+        for (int c = 0; c < 6; ++c) acc[c] = 0.0;
+        for (int c = 0; c < 6; ++c) hs[c] = warp_sum(hs[c]);
     }
-    for (int k = 0; k < 4; ++k) P.quat_old[4 * t + k] = q[k];
-
-    double F[3], M[3];
-    bool finite = true;
-    for (int k = 0; k < 3; ++k) {
-        F[k] = hs[k] + eF[k];
-        M[k] = hs[3 + k] + eM[k];
-        finite = finite && isfinite(F[k]) && isfinite(M[k]);
+    const double hF = sel3(k, hs[0], hs[1], hs[2]), hM = sel3(k, hs[3], hs[4], hs[5]);
+    if (vec) {
+        P.last[6 * t + k] = hF;
+        P.last[6 * t + 3 + k] = hM;
+        P.pos_old[3 * t + k] = pos;
+        P.vel_old[3 * t + k] = vel;
+        P.om_old[3 * t + k] = om;
     }
-    float hold[3];
-    const double cold[3] = {pos[0], pos[1], pos[2]};
-    aabb_half(Rold, semi, hold);
-
+    if (lane < 4) P.quat_old[4 * t + lane] = lane == 0 ? w : sel3(lane - 1, x, y, z);
+    const double F = hF + eF, M = hM + eM;
+    bool finite = isfinite(F) && isfinite(M);
+    // old box half extent along k (FP32; the box only has to contain the body)
+    const float sf0 = (float)s0, sf1 = (float)s1, sf2 = (float)s2;
+    auto half = [&](float r0, float r1, float r2) {
+        const float e0 = r0 * sf0, e1 = r1 * sf1, e2 = r2 * sf2;
+        return sqrtf(e0 * e0 + e1 * e1 + e2 * e2) * 1.0001f;
+    };
+    const float hold = half((float)Rr0, (float)Rr1, (float)Rr2);
+    double posn = pos, veln = vel, omn = om, Ln = Lm, wn = w, xn = x, yn = y, zn = z;
     if (!fixed) {
         // divisions are replaced by the host's reciprocals of mass and inertia
-        for (int k = 0; k < 3; ++k) vel[k] += F[k] * minv;
-        for (int k = 0; k < 3; ++k) pos[k] += vel[k];
-        for (int k = 0; k < 3; ++k) Lm[k] += M[k];
+        veln = vel + F * minv;
+        posn = pos + veln;
+        Ln = Lm + M;
         // omega = R diag(1/I) R^T L with the orientation before the update
-        double lb[3];
-        for (int k = 0; k < 3; ++k)
-            lb[k] = (Rold[k] * Lm[0] + Rold[3 + k] * Lm[1] + Rold[6 + k] * Lm[2]) * Iinv[k];
-        for (int k = 0; k < 3; ++k)
-            om[k] = Rold[3 * k] * lb[0] + Rold[3 * k + 1] * lb[1] + Rold[3 * k + 2] * lb[2];
-        const double th2 = om[0] * om[0] + om[1] * om[1] + om[2] * om[2];
+        const double L0 = __shfl_sync(full, Ln, 0), L1 = __shfl_sync(full, Ln, 1), L2 = __shfl_sync(full, Ln, 2);
+        const double lb = (Rc0 * L0 + Rc1 * L1 + Rc2 * L2) * Iinv;
+        const double b0 = __shfl_sync(full, lb, 0), b1 = __shfl_sync(full, lb, 1), b2 = __shfl_sync(full, lb, 2);
+        omn = Rr0 * b0 + Rr1 * b1 + Rr2 * b2;
+        const double o0 = __shfl_sync(full, omn, 0), o1 = __shfl_sync(full, omn, 1), o2 = __shfl_sync(full, omn, 2);
+        const double th2 = o0 * o0 + o1 * o1 + o2 * o2;
         // exp(Omega/2) = (cos(th/2), sin(th/2) Omega/th); for the small angles of
         // one lattice step the Maclaurin series of cos x and sin x / x in
         // x^2 = th^2/4, truncated after x^8 (remainder < 1e-19 for th < 0.02)
@@ -254,78 +254,77 @@ __global__ void rigid_body_kernel(RemapArgs a) {
             sincos(0.5 * th, &sh, &ch);
             shr = sh / th;
         }
-        const double dq[4] = {ch, om[0] * shr, om[1] * shr, om[2] * shr};
-        double nq[4];
-        nq[0] = dq[0] * q[0] - (dq[1] * q[1] + dq[2] * q[2] + dq[3] * q[3]);
-        nq[1] = dq[0] * q[1] + q[0] * dq[1] + (dq[2] * q[3] - dq[3] * q[2]);
-        nq[2] = dq[0] * q[2] + q[0] * dq[2] + (dq[3] * q[1] - dq[1] * q[3]);
-        nq[3] = dq[0] * q[3] + q[0] * dq[3] + (dq[1] * q[2] - dq[2] * q[1]);
-        // renormalise: a product of unit quaternions has |nq|^2 = 1 + d with d
+        const double d0 = ch, d1 = o0 * shr, d2 = o1 * shr, d3 = o2 * shr;
+        const double n0 = d0 * w - (d1 * x + d2 * y + d3 * z);
+        const double n1 = d0 * x + w * d1 + (d2 * z - d3 * y);
+        const double n2 = d0 * y + w * d2 + (d3 * x - d1 * z);
+        const double n3 = d0 * z + w * d3 + (d1 * y - d2 * x);
+        // renormalise: a product of unit quaternions has |n|^2 = 1 + d with d
         // at rounding level, and one Newton step for 1/sqrt from 1 gives
-        // 1.5 - 0.5 |nq|^2, exact to O(d^2)
-        const double n2 = nq[0] * nq[0] + nq[1] * nq[1] + nq[2] * nq[2] + nq[3] * nq[3];
-        const double rn = fabs(n2 - 1.0) < 1e-6 ? 1.5 - 0.5 * n2 : 1.0 / sqrt(n2);
-        for (int k = 0; k < 4; ++k) q[k] = nq[k] * rn;
-        for (int k = 0; k < 3; ++k)
-            if (per[k]) {
-                if (pos[k] >= dims[k])
-                    pos[k] -= dims[k];
-                else if (pos[k] < 0.0)
-                    pos[k] += dims[k];
-            }
-        for (int k = 0; k < 3; ++k) finite = finite && isfinite(pos[k]) && isfinite(om[k]);
-        for (int k = 0; k < 3; ++k) {
-            P.pos[3 * t + k] = pos[k];
-            P.vel[3 * t + k] = vel[k];
-            P.om[3 * t + k] = om[k];
-            P.L[3 * t + k] = Lm[k];
+        // 1.5 - 0.5 |n|^2, exact to O(d^2)
+        const double nn = n0 * n0 + n1 * n1 + n2 * n2 + n3 * n3;
+        const double rn = fabs(nn - 1.0) < 1e-6 ? 1.5 - 0.5 * nn : 1.0 / sqrt(nn);
+        wn = n0 * rn;
+        xn = n1 * rn;
+        yn = n2 * rn;
+        zn = n3 * rn;
+        if (per) {
+            if (posn >= dim)
+                posn -= dim;
+            else if (posn < 0.0)
+                posn += dim;
         }
-        for (int k = 0; k < 4; ++k) P.quat[4 * t + k] = q[k];
+        finite = finite && isfinite(posn) && isfinite(omn);
     }
-    if (!finite) atomicOr(a.err, ERR_NONFINITE);
-
-    // rotation of the new orientation, rounded as the mapping's exact inside
-    // test expects; FP32 copies of the new pose and motion for the
-    // re-mapping pre-test and the sweep's bounce-back (reciprocal semi-axes
-    // are set once, on the host)
-    double Rnew[9];
-    quat_matrix_rn(q, Rnew);
-    for (int k = 0; k < 9; ++k) P.R64[9 * (size_t)t + k] = Rnew[k];
-    float hnew[3];
-    aabb_half(Rnew, semi, hnew);
-    float *bf = P.bodyf + BF_STRIDE * (size_t)t;
-    for (int k = 0; k < 9; ++k) bf[BF_R + k] = (float)Rnew[k];
-    float posf[3], coldf[3];
-    for (int k = 0; k < 3; ++k) {
-        const df c = df_from_double(pos[k]);
-        bf[BF_POS + k] = c.hi;
-        bf[BF_POSLO + k] = c.lo;
-        bf[BF_U + k] = (float)vel[k];
-        bf[BF_W + k] = (float)om[k];
-        posf[k] = c.hi;
-        coldf[k] = (float)cold[k];
+    if (!__all_sync(full, finite) && lane == 0) atomicOr(a.err, ERR_NONFINITE);
+    // rotation of the new orientation (lane e < 9: entry e), rounded as the
+    // mapping's exact inside test expects, and its FP32 copy
+    const double Re = quat_entry_rn(lane < 9 ? lane : 0, wn, xn, yn, zn);
+    const float Rf = (float)Re;
+    float *bf = P.bodyf + BF_STRIDE * t;
+    if (lane < 9) {
+        P.R64[9 * t + lane] = Re;
+        bf[BF_R + lane] = Rf;
     }
-    // re-mapping box: union of the old and new bounding boxes plus a margin
-    // of two cells, in FP32 with a slack far above its rounding
-    for (int k = 0; k < 3; ++k) {
-        float lo = fminf(coldf[k] - hold[k], posf[k] - hnew[k]) - 1e-3f;
-        float hi = fmaxf(coldf[k] + hold[k], posf[k] + hnew[k]) + 1e-3f;
-        // a wrapped centre makes the two boxes an image apart: use the new one
-        if (per[k] && fabsf(coldf[k] - posf[k]) > 0.5f * (float)dims[k]) {
-            lo = fminf(posf[k] - hnew[k], posf[k] - hold[k]) - 1e-3f;
-            hi = fmaxf(posf[k] + hnew[k], posf[k] + hold[k]) + 1e-3f;
+    const float hnew = half(__shfl_sync(full, Rf, 3 * k), __shfl_sync(full, Rf, 3 * k + 1),
+                            __shfl_sync(full, Rf, 3 * k + 2));
+    if (!fixed) {
+        if (vec) {
+            P.pos[3 * t + k] = posn;
+            P.vel[3 * t + k] = veln;
+            P.om[3 * t + k] = omn;
+            P.L[3 * t + k] = Ln;
         }
-        int ilo = (int)floorf(lo) - 2, ihi = (int)ceilf(hi) + 2;
-        if (!isfinite(lo) || !isfinite(hi)) { ilo = 0; ihi = -1; }
-        if (per[k]) {
-            if (ihi - ilo + 1 > dims[k]) { ilo = 0; ihi = dims[k] - 1; }
-        } else {
-            ilo = max(ilo, 0);
-            ihi = min(ihi, dims[k] - 1);
-        }
-        P.region[6 * t + k] = ilo;
-        P.region[6 * t + 3 + k] = max(ihi - ilo + 1, 0);
+        if (lane < 4) P.quat[4 * t + lane] = lane == 0 ? wn : sel3(lane - 1, xn, yn, zn);
     }
+    if (!vec) return;
+    // FP32 copies of the new centre (double-float), velocity and angular
+    // velocity for the re-mapping pre-test and the sweep's bounce-back
+    const df c = df_from_double(posn);
+    bf[BF_POS + k] = c.hi;
+    bf[BF_POSLO + k] = c.lo;
+    bf[BF_U + k] = (float)veln;
+    bf[BF_W + k] = (float)omn;
+    // re-mapping box along k: union of the old and new bounding boxes plus a
+    // margin of two cells, in FP32 with a slack far above its rounding
+    const float posf = c.hi, coldf = (float)pos;
+    float lo = fminf(coldf - hold, posf - hnew) - 1e-3f;
+    float hi = fmaxf(coldf + hold, posf + hnew) + 1e-3f;
+    // a wrapped centre makes the two boxes an image apart: use the new one
+    if (per && fabsf(coldf - posf) > 0.5f * (float)dim) {
+        lo = fminf(posf - hnew, posf - hold) - 1e-3f;
+        hi = fmaxf(posf + hnew, posf + hold) + 1e-3f;
+    }
+    int ilo = (int)floorf(lo) - 2, ihi = (int)ceilf(hi) + 2;
+    if (!isfinite(lo) || !isfinite(hi)) { ilo = 0; ihi = -1; }
+    if (per) {
+        if (ihi - ilo + 1 > dim) { ilo = 0; ihi = dim - 1; }
+    } else {
+        ilo = max(ilo, 0);
+        ihi = min(ihi, dim - 1);
+    }
+    P.region[6 * t + k] = ilo;
+    P.region[6 * t + 3 + k] = max(ihi - ilo + 1, 0);
 }
 
 // ---------------------------------------------------------------------------
