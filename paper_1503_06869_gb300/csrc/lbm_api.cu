@@ -38,6 +38,8 @@ struct lbm_ctx {
     uint32_t *pid = nullptr, *pid_prev = nullptr;
     double *wall_acc = nullptr, *wall_last = nullptr;
     uint32_t *tbits = nullptr;      // direct sweep: tiles that may hold non-bulk cells
+    uint64_t *links = nullptr;      // per-cell link words (neighbour masks)
+    uint32_t *nbody = nullptr;      // per-cell first neighbouring body
     __half *cl_par = nullptr;       // learned closure: FP16 network parameters
     bool closure = false;
     uint32_t *err = nullptr;
@@ -176,6 +178,8 @@ SweepArgs sweep_args(lbm_ctx *ctx) {
     a.wall_acc = ctx->wall_acc;
     a.err = ctx->err;
     a.tbits = ctx->variant == SWEEP_DIRECT ? ctx->tbits : nullptr;
+    a.links = ctx->links;
+    a.nbody = ctx->nbody;
     return a;
 }
 
@@ -193,6 +197,8 @@ RemapArgs remap_args(lbm_ctx *ctx) {
     a.err = ctx->err;
     a.tbits = ctx->variant == SWEEP_DIRECT ? ctx->tbits : nullptr;
     a.tile = tile_cells(ctx);
+    a.links = ctx->links;
+    a.nbody = ctx->nbody;
     return a;
 }
 
@@ -456,6 +462,8 @@ lbm_status create_common(const lbm_grid_desc *cells, int ncells, lbm_ctx **out) 
     ctx->flags = (uint8_t *)owned_alloc(ctx, (size_t)coff);
     ctx->pid = (uint32_t *)owned_alloc(ctx, (size_t)coff * 4);
     ctx->pid_prev = (uint32_t *)owned_alloc(ctx, (size_t)coff * 4);
+    ctx->links = (uint64_t *)owned_alloc(ctx, (size_t)coff * 8);
+    ctx->nbody = (uint32_t *)owned_alloc(ctx, (size_t)coff * 4);
     ctx->wall_acc = (double *)owned_alloc(ctx, sizeof(double) * 6 * ACC_COPIES * ncells);
     ctx->wall_last = (double *)owned_alloc(ctx, sizeof(double) * 6 * ncells);
     ctx->err = (uint32_t *)owned_alloc(ctx, 16);
@@ -465,7 +473,7 @@ lbm_status create_common(const lbm_grid_desc *cells, int ncells, lbm_ctx **out) 
         ctx->tbits = (uint32_t *)owned_alloc(ctx, sizeof(uint32_t) * (size_t)(tiles32 / 32 + 1));
     }
     if (!ctx->lat_d || !ctx->f || !ctx->flags || !ctx->pid || !ctx->pid_prev || !ctx->wall_acc ||
-        !ctx->wall_last || !ctx->err || !ctx->tbits) {
+        !ctx->wall_last || !ctx->err || !ctx->tbits || !ctx->links || !ctx->nbody) {
         lbm_destroy(ctx);
         return LBM_ERR_OOM;
     }
@@ -486,7 +494,8 @@ lbm_status create_common(const lbm_grid_desc *cells, int ncells, lbm_ctx **out) 
         return LBM_ERR_CUDA;
     }
     for (int i = 0; i < ncells; ++i) {
-        if (launch_init_cells(ctx->lat_h[i], ctx->lat_d + i, ctx->flags, ctx->pid, ctx->pid_prev,
+        if (launch_init_cells(ctx->lat_h[i], ctx->lat_d + i, ctx->flags, ctx->pid, ctx->pid_prev, ctx->links,
+                              ctx->nbody,
                               ctx->stream) != cudaSuccess) {
             lbm_destroy(ctx);
             return LBM_ERR_CUDA;

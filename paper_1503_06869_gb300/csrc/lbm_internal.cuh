@@ -149,6 +149,8 @@ struct SweepArgs {
     // flag; a clear bit guarantees that every cell of the tile is bulk fluid
     // (null: every tile is treated as flagged)
     const uint32_t *tbits;
+    const uint64_t *links;   // per cell: neighbour masks (LK_* layout)
+    const uint32_t *nbody;   // per cell: first body among the neighbours
 };
 
 // Storage forms: every form holds g_q = f_q - w_q rho0 (the offset from rest).
@@ -303,6 +305,14 @@ cudaError_t launch_to_half(const float *src, __half *dst, int n, cudaStream_t s)
 int sweep_max_active_blocks(int prec, int variant, int block);
 constexpr int STAGED_TILE = 256;
 
+// Link word of a fluid cell (PartDev-independent, kept by the flags pass):
+// bit q (1..18) of each 19-bit field refers to the neighbour x + c_q --
+// field 0: wall or obstacle cell, field 1: wall-layer cell, field 2: cell of
+// the first body met in q order (whose id is kept in nbody).  Zero for cells
+// without wall or obstacle neighbours and for solid cells.
+constexpr int LK_WALL = 19, LK_BODY = 38;
+constexpr uint32_t LK_MASK = 0x7FFFFu;
+
 struct RemapArgs {
     const LatDev *lat;
     void *f;
@@ -316,6 +326,8 @@ struct RemapArgs {
     uint32_t *err;
     uint32_t *tbits;     // direct-sweep tile bits (may be null)
     int tile;            // cells per direct-sweep tile
+    uint64_t *links;     // per-cell link words (LK_* layout)
+    uint32_t *nbody;     // per-cell first neighbouring body
 };
 // Recount every tile bit from the flags (bit t = tile t holds a nonzero flag).
 cudaError_t launch_tile_bits(const RemapArgs &a, int ntiles, cudaStream_t s);
@@ -328,7 +340,7 @@ cudaError_t launch_claim_all(const RemapArgs &a, int blocks_per_body, cudaStream
 cudaError_t launch_remap_full(int prec, int next_parity, const RemapArgs &a, const LatDev &h,
                               int lat_index, cudaStream_t s);
 cudaError_t launch_init_cells(const LatDev &h, const LatDev *d, uint8_t *flags, uint32_t *pid,
-                              uint32_t *pid_prev, cudaStream_t s);
+                              uint32_t *pid_prev, uint64_t *links, uint32_t *nbody, cudaStream_t s);
 cudaError_t launch_canonical(int prec, int next_parity, const LatDev &h, const LatDev *d,
                              const void *f, const uint8_t *flags, const uint32_t *pid,
                              double *rho, double *u3, uint8_t *flags_out, double *pdfs,

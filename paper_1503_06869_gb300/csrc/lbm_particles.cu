@@ -517,16 +517,28 @@ __global__ void fixup_region_kernel(RemapArgs a, int bpb) {
     }
 }
 
+// Flag byte of cell (i,j,k) from the particle-id map, and for a fluid cell
+// its link word (LK_* layout) and the first body among its neighbours.
 __device__ __forceinline__ uint8_t flag_of(const LatDev &L, const uint32_t *pid, long long coff, int i,
-                                           int j, int k) {
+                                           int j, int k, uint64_t &links, uint32_t &p0) {
+    links = 0;
+    p0 = PID_FLUID;
     const uint32_t id = pid[coff + i + L.nx * (j + L.ny * k)];
     if (id != PID_FLUID) return id >= PID_WALL ? (F_SOLID | F_WALL) : F_SOLID;
     bool near = false, only_lo = true, only_hi = true;
+    uint32_t solid = 0, wall = 0, body = 0;
 #pragma unroll
     for (int q = 1; q < Q; ++q) {
         const int n = lin(L, i + cx(q), j + cy(q), k + cz(q));
         const uint32_t nid = pid[coff + n];
         if (nid != PID_FLUID) {
+            solid |= 1u << q;
+            if (nid >= PID_WALL) {
+                wall |= 1u << q;
+            } else {
+                if (p0 == PID_FLUID) p0 = nid;
+                if (nid == p0) body |= 1u << q;
+            }
             near = true;
             // a wall cell hit along c_q must be in the layer c_q points to
             only_lo = only_lo && nid == PID_WALL_YLO && cy(q) < 0;
@@ -538,6 +550,7 @@ __device__ __forceinline__ uint8_t flag_of(const LatDev &L, const uint32_t *pid,
         }
     }
     if (!near) return 0;
+    links = (uint64_t)solid | ((uint64_t)wall << LK_WALL) | ((uint64_t)body << LK_BODY);
     if (only_lo && j == 1 && !L.py) return F_NEAR | F_YLO;
     if (only_hi && j == L.ny - 2 && !L.py) return F_NEAR | F_YHI;
     return F_NEAR;
@@ -557,8 +570,12 @@ __global__ void flags_region_kernel(RemapArgs a, int bpb) {
         region_cell(reg, L, r, c);
         const long long cg = L.c_off + c.idx;
         if (a.flags[cg] & F_WALL) continue;
-        const uint8_t f = flag_of(L, a.pid, L.c_off, c.i, c.j, c.k);
+        uint64_t lk;
+        uint32_t p0;
+        const uint8_t f = flag_of(L, a.pid, L.c_off, c.i, c.j, c.k, lk, p0);
         a.flags[cg] = f;
+        a.links[cg] = lk;
+        a.nbody[cg] = p0;
         // a cell turning non-bulk marks its tile; marks are cleared only by a
         // recount (launch_tile_bits), so a stale mark costs the flagged path,
         // never a missed cell
@@ -617,12 +634,17 @@ __global__ void init_pid_kernel(const LatDev *lat, uint32_t *pid, uint32_t *pid_
     pid_prev[L.c_off + x] = PID_FLUID;
 }
 
-__global__ void flags_full_kernel(const LatDev *lat, uint8_t *flags, const uint32_t *pid) {
+__global__ void flags_full_kernel(const LatDev *lat, uint8_t *flags, const uint32_t *pid, uint64_t *links,
+                                  uint32_t *nbody) {
     const LatDev &L = *lat;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= L.n) return;
     const int i = x % L.nx, j = (x / L.nx) % L.ny, k = x / (L.nx * L.ny);
-    flags[L.c_off + x] = flag_of(L, pid, L.c_off, i, j, k);
+    uint64_t lk;
+    uint32_t p0;
+    flags[L.c_off + x] = flag_of(L, pid, L.c_off, i, j, k, lk, p0);
+    links[L.c_off + x] = lk;
+    nbody[L.c_off + x] = p0;
 }
 
 __global__ void clear_particles_kernel(const LatDev *lat, uint8_t *flags, uint32_t *pid, uint32_t *pid_prev) {
@@ -830,7 +852,7 @@ cudaError_t remap_full_prec(int next_parity, const RemapArgs &a, const LatDev &h
         fixup_full_kernel<PREC, 1><<<nb, REMAP_BLOCK, 0, s>>>(a, d);
     else
         fixup_full_kernel<PREC, 0><<<nb, REMAP_BLOCK, 0, s>>>(a, d);
-    flags_full_kernel<<<nb, REMAP_BLOCK, 0, s>>>(d, a.flags, a.pid);
+    flags_full_kernel<<<nb, REMAP_BLOCK, 0, s>>>(d, a.flags, a.pid, a.links, a.nbody);
     return cudaGetLastError();
 }
 
@@ -920,10 +942,10 @@ cudaError_t launch_remap_full(int prec, int next_parity, const RemapArgs &a, con
 }
 
 cudaError_t launch_init_cells(const LatDev &h, const LatDev *d, uint8_t *flags, uint32_t *pid,
-                              uint32_t *pid_prev, cudaStream_t s) {
+                              uint32_t *pid_prev, uint64_t *links, uint32_t *nbody, cudaStream_t s) {
     const int nb = (h.n + 255) / 256;
     init_pid_kernel<<<nb, 256, 0, s>>>(d, pid, pid_prev);
-    flags_full_kernel<<<nb, 256, 0, s>>>(d, flags, pid);
+    flags_full_kernel<<<nb, 256, 0, s>>>(d, flags, pid, links, nbody);
     return cudaGetLastError();
 }
 

@@ -413,29 +413,17 @@ __device__ __forceinline__ void near_cell(const SweepArgs &a, const LatDev &L, i
     const long long np = L.npad;
     const T *stage = reinterpret_cast<const T *>(src);
     const typename RingCfg<PREC>::Word *col = reinterpret_cast<const typename RingCfg<PREC>::Word *>(src);
-    uint32_t solid = 0;  // bit q: x + c_q is a wall or obstacle cell
-    uint32_t wall = 0;   // bit q: x + c_q is a wall-layer cell
-#pragma unroll
-    for (int q = 1; q < Q; ++q) {
-        const uint8_t f = a.flags[L.c_off + idx + nb_off(cg, q)];
-        if (f & F_SOLID) solid |= 1u << q;
-        if (f & F_WALL) wall |= 1u << q;
-    }
+    // the flags pass keeps, per fluid cell, which neighbours are wall or
+    // obstacle cells, which of them are wall-layer cells and which belong to
+    // the first body met in q order (p0)
+    const uint64_t lk = a.links[L.c_off + idx];
+    const uint32_t solid = (uint32_t)lk & LK_MASK;            // bit q: x + c_q is a wall or obstacle cell
+    const uint32_t wall = (uint32_t)(lk >> LK_WALL) & LK_MASK;  // bit q: x + c_q is a wall-layer cell
+    const uint32_t m0 = (uint32_t)(lk >> LK_BODY) & LK_MASK;    // bit q: x + c_q is a cell of body p0
     // Obstacle links: the first body met (p0) has its motion loaded once and
     // its links are bounced inline in the compute precision, their momentum
-    // summed per cell; links to any further body take bounce_link.  The
-    // ids and the body's motion are settled before the populations are
-    // loaded, so that only the populations and the sums stay live through
-    // the link loop (the path runs under the sweep's register budget).
-    const uint32_t obst = solid & ~wall;
-    uint32_t p0 = SLOT_EMPTY, m0 = 0;
-#pragma unroll
-    for (int q = 1; q < Q; ++q)
-        if ((obst >> q) & 1u) {
-            const uint32_t id = a.pid[L.c_off + idx + nb_off(cg, q)];
-            if (p0 == SLOT_EMPTY) p0 = id;
-            if (id == p0) m0 |= 1u << q;
-        }
+    // summed per cell; links to any further body take bounce_link.
+    const uint32_t p0 = m0 ? a.nbody[L.c_off + idx] : SLOT_EMPTY;
     // body p0: lever arm r_F of this cell (compute precision), velocity U and
     // angular velocity W
     using A = Acc<PREC>;
