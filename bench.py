@@ -333,7 +333,7 @@ def main():
                     "h2d_bytes_per_step": 24 * len(w.particles),
                     "d2h_bytes_per_step": 48 * len(w.particles)},
             "gpu_launches": int(launches),
-            "launch": {"block": info.sweep_block, "grid": info.sweep_grid},
+            "launch": {"block": info.sweep_block, "grid": info.sweep_grid, "split": bool(info.sweep_split)},
             "clocks": clk}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)

@@ -59,8 +59,9 @@ typedef enum lbm_status {
 
 /* How populations are stored in device memory.  Every form stores the offset
  * g_q = f_q - w_q*rho0 from the rest state.  F64 computes in double; the others
- * compute in float.  Force/torque sums and the rigid-body update are always
- * double. */
+ * compute in float.  The force/torque accumulators and the rigid-body update
+ * are always double; on the float forms the per-cell and per-warp partial
+ * sums before them are compensated float pairs (about 48 bits). */
 typedef enum lbm_precision {
     LBM_F64 = 0,
     LBM_F32 = 1,
@@ -224,6 +225,7 @@ typedef struct lbm_info {
     size_t device_bytes;        /* device memory held by the context */
     int sweep_grid, sweep_block;/* launch shape of the sweep kernel */
     int bytes_per_population;   /* 8, 4 or 2 */
+    int sweep_split;            /* 1: the direct sweep runs split (lbm_set_sweep_split) */
 } lbm_info;
 
 lbm_status lbm_get_info(lbm_ctx *ctx, lbm_info *info);
@@ -239,6 +241,15 @@ lbm_status lbm_get_info(lbm_ctx *ctx, lbm_info *info);
  * effect at the next lbm_step.  Any other block value returns LBM_ERR_ARG.
  * The default is the direct sweep with 128 threads. */
 lbm_status lbm_set_launch(lbm_ctx *ctx, int block, int grid);
+
+/* Split direct sweep (enable != 0): near-obstacle cells (those next to a
+ * body or a resting wall) leave the sweep kernel; a list kernel compacts them
+ * from the marked tiles and a third kernel updates them, one cell per
+ * thread, so that warps in the near-obstacle path are full.  The two kernels
+ * touch disjoint population slots.  Worth it when bodies are many (dense
+ * suspensions); the autotuner decides.  Applies to the direct sweep only;
+ * takes effect at the next lbm_step. */
+lbm_status lbm_set_sweep_split(lbm_ctx *ctx, int enable);
 
 /* Choose the sweep launch shape by timing candidates on this context (runs
  * sweeps on scratch copies: the state is restored afterwards).  The chosen

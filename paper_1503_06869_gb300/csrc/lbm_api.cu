@@ -40,6 +40,9 @@ struct lbm_ctx {
     uint32_t *tbits = nullptr;      // direct sweep: tiles that may hold non-bulk cells
     uint64_t *links = nullptr;      // per-cell link words (neighbour masks)
     uint32_t *nbody = nullptr;      // per-cell first neighbouring body
+    uint32_t *near_list = nullptr;  // split direct sweep: compacted near-obstacle cells
+    uint32_t *near_count = nullptr;
+    bool split = false;             // direct sweep: near-obstacle cells in a kernel of their own
     __half *cl_par = nullptr;       // learned closure: FP16 network parameters
     bool closure = false;
     uint32_t *err = nullptr;
@@ -180,8 +183,14 @@ SweepArgs sweep_args(lbm_ctx *ctx) {
     a.tbits = ctx->variant == SWEEP_DIRECT ? ctx->tbits : nullptr;
     a.links = ctx->links;
     a.nbody = ctx->nbody;
+    const bool split = ctx->split && ctx->variant == SWEEP_DIRECT;
+    a.near_list = split ? ctx->near_list : nullptr;
+    a.near_count = split ? ctx->near_count : nullptr;
     return a;
 }
+
+// kernels one sweep issues (the split direct sweep: list, sweep, near cells)
+int sweep_kernels(const lbm_ctx *ctx) { return (ctx->split && ctx->variant == SWEEP_DIRECT) ? 3 : 1; }
 
 RemapArgs remap_args(lbm_ctx *ctx) {
     RemapArgs a;
@@ -274,7 +283,7 @@ lbm_status enqueue_step(lbm_ctx *ctx, bool timed) {
     }
     RemapArgs ra = remap_args(ctx);
     CK(launch_rigid_body(ra, ctx->stream));
-    ctx->launches += 2;
+    ctx->launches += sweep_kernels(ctx) + 1;
     if (ctx->np > 0) {
         CK(launch_remap_step(ctx->prec, 1 - parity, ra, ctx->remap_bpb, ctx->stream));
         ctx->launches += kernels_per_remap_step();
@@ -464,6 +473,8 @@ lbm_status create_common(const lbm_grid_desc *cells, int ncells, lbm_ctx **out) 
     ctx->pid_prev = (uint32_t *)owned_alloc(ctx, (size_t)coff * 4);
     ctx->links = (uint64_t *)owned_alloc(ctx, (size_t)coff * 8);
     ctx->nbody = (uint32_t *)owned_alloc(ctx, (size_t)coff * 4);
+    ctx->near_list = (uint32_t *)owned_alloc(ctx, (size_t)coff * 4);
+    ctx->near_count = (uint32_t *)owned_alloc(ctx, 16);
     ctx->wall_acc = (double *)owned_alloc(ctx, sizeof(double) * 6 * ACC_COPIES * ncells);
     ctx->wall_last = (double *)owned_alloc(ctx, sizeof(double) * 6 * ncells);
     ctx->err = (uint32_t *)owned_alloc(ctx, 16);
@@ -473,7 +484,8 @@ lbm_status create_common(const lbm_grid_desc *cells, int ncells, lbm_ctx **out) 
         ctx->tbits = (uint32_t *)owned_alloc(ctx, sizeof(uint32_t) * (size_t)(tiles32 / 32 + 1));
     }
     if (!ctx->lat_d || !ctx->f || !ctx->flags || !ctx->pid || !ctx->pid_prev || !ctx->wall_acc ||
-        !ctx->wall_last || !ctx->err || !ctx->tbits || !ctx->links || !ctx->nbody) {
+        !ctx->wall_last || !ctx->err || !ctx->tbits || !ctx->links || !ctx->nbody || !ctx->near_list ||
+        !ctx->near_count) {
         lbm_destroy(ctx);
         return LBM_ERR_OOM;
     }
@@ -742,7 +754,8 @@ lbm_status lbm_step(lbm_ctx *ctx, int nsteps) {
                 lbm_status s = build_graph(ctx);
                 if (s != LBM_OK) return s;
             }
-            const int per = 2 * (2 + closure_kernels(ctx) + (ctx->np > 0 ? kernels_per_remap_step() : 0));
+            const int per =
+                2 * (sweep_kernels(ctx) + 1 + closure_kernels(ctx) + (ctx->np > 0 ? kernels_per_remap_step() : 0));
             while (left >= 2) {
                 CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
                 ctx->t += 2;
@@ -991,6 +1004,7 @@ lbm_status lbm_get_info(lbm_ctx *ctx, lbm_info *info) {
     info->sweep_grid = ctx->grid;
     info->sweep_block = ctx->variant == SWEEP_RING ? 0 : (ctx->variant == SWEEP_STAGED ? -1 : ctx->block);
     info->bytes_per_population = ctx->esize;
+    info->sweep_split = (ctx->split && ctx->variant == SWEEP_DIRECT) ? 1 : 0;
     return LBM_OK;
 }
 
@@ -1024,18 +1038,21 @@ lbm_status lbm_autotune(lbm_ctx *ctx, int *block_out, int *grid_out) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     // candidates: the ring sweep (block 0), the staged sweep (block -1) and
-    // the direct sweep at two block sizes, each with persistent grids (1x, 2x
-    // resident) and one tile per block
-    const int blocks[] = {0, -1, 128, 256};
+    // the direct sweep at two block sizes, fused or split, each with
+    // persistent grids (1x, 2x resident) and one tile per block
+    const int blocks[] = {0, -1, 128, 256, 128 + 1024, 256 + 1024};  // +1024: split direct sweep
     double best = 1e30;
     int bb = ctx->variant == SWEEP_RING ? 0 : (ctx->variant == SWEEP_STAGED ? -1 : ctx->block);
     int bg = ctx->grid;
+    bool bsplit = ctx->split;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    for (int blk : blocks) {
+    for (int cand : blocks) {
+        const int blk = cand > 1024 ? cand - 1024 : cand;
         lbm_status s = lbm_set_launch(ctx, blk, 0);
         if (s != LBM_OK) break;
+        ctx->split = cand > 1024;
         const int occ = sweep_max_active_blocks(ctx->prec, ctx->variant, ctx->block);
         if (occ <= 0) continue;
         const int grids[] = {sms * occ, 2 * sms * occ, ctx->ntiles};
@@ -1055,18 +1072,20 @@ lbm_status lbm_autotune(lbm_ctx *ctx, int *block_out, int *grid_out) {
             }
             CK(cudaEventRecord(e1, ctx->stream));
             CK(cudaEventSynchronize(e1));
-            ctx->launches += 2 * (2 + reps);
+            ctx->launches += 2 * (2 + reps) * sweep_kernels(ctx);
             float ms = 0.f;
             CK(cudaEventElapsedTime(&ms, e0, e1));
             if (ms < best) {
                 best = ms;
                 bb = blk;
                 bg = gr;
+                bsplit = ctx->split;
             }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    ctx->split = bsplit;
     lbm_status s = lbm_set_launch(ctx, bb, bg);
     CK(cudaMemcpyAsync(ctx->f, backup, fbytes, cudaMemcpyDeviceToDevice, ctx->stream));
     if (ctx->np > 0) CK(cudaMemsetAsync(ctx->P.acc, 0, sizeof(double) * 6 * ACC_COPIES * ctx->np, ctx->stream));
@@ -1076,6 +1095,14 @@ lbm_status lbm_autotune(lbm_ctx *ctx, int *block_out, int *grid_out) {
     if (block_out) *block_out = bb;
     if (grid_out) *grid_out = bg;
     return s;
+}
+
+lbm_status lbm_set_sweep_split(lbm_ctx *ctx, int enable) {
+    if (!ctx) return LBM_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->split = enable != 0;
+    drop_graph(ctx);
+    return LBM_OK;
 }
 
 lbm_status lbm_set_graphs(lbm_ctx *ctx, int enable) {

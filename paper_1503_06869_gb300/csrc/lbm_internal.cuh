@@ -151,6 +151,12 @@ struct SweepArgs {
     const uint32_t *tbits;
     const uint64_t *links;   // per cell: neighbour masks (LK_* layout)
     const uint32_t *nbody;   // per cell: first body among the neighbours
+    // split direct sweep (null: near cells stay in the sweep): the sweep skips
+    // near-obstacle cells, a list kernel compacts them into near_list
+    // (global cell indices, *near_count of them) and a second kernel
+    // updates them with every lane busy
+    uint32_t *near_list;
+    uint32_t *near_count;
 };
 
 // Storage forms: every form holds g_q = f_q - w_q rho0 (the offset from rest).

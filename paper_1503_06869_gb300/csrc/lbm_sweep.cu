@@ -718,6 +718,7 @@ __global__ void __launch_bounds__(256, SweepBounds<PREC>::MINB)
             continue;
         }
         if (fl & F_NEAR) {
+            if (a.near_list) continue;  // split sweep: the near kernel updates it
             near_cell<PREC, ODD, 3>(a, L, li, idx, &tkey[threadIdx.x], tval[threadIdx.x], nullptr, g);
             continue;
         }
@@ -1074,6 +1075,65 @@ __global__ void __launch_bounds__(256, SweepBounds<PREC>::MINB)
 
 // variant: SWEEP_DIRECT (one cell per thread, `block` threads), SWEEP_STAGED
 // (bulk-copy pipeline), SWEEP_RING (per-thread cp.async prefetch ring).
+// Split sweep, step 1: the near-obstacle cells (F_NEAR without a flat-wall
+// flag) of the tiles marked in the tile bits, compacted into a.near_list --
+// one warp per 32 cells of a tile, one atomic per warp.  T = cells per tile.
+template <bool SINGLE>
+__global__ void near_list_kernel(const __grid_constant__ SweepArgs a, int T) {
+    pdl_enter();
+    const int lane = threadIdx.x & 31;
+    const long long wpb = blockDim.x >> 5;
+    const long long chunks = T >> 5;
+    const long long total = (long long)a.ntiles * chunks;
+    for (long long w = blockIdx.x * wpb + (threadIdx.x >> 5); w < total; w += (long long)gridDim.x * wpb) {
+        const int tile = (int)(w / chunks), ch = (int)(w - (long long)tile * chunks);
+        if (a.tbits && !((a.tbits[tile >> 5] >> (tile & 31)) & 1u)) continue;  // uniform per warp
+        const int li = tile_lattice<SINGLE>(a, tile);
+        const LatDev &L = SINGLE ? a.lat0 : a.lat[li];
+        const int idx = (tile - L.tile0) * T + ch * 32 + lane;
+        bool nearc = false;
+        if (idx < L.n) {
+            const uint8_t fl = a.flags[L.c_off + idx];
+            nearc = (fl & F_NEAR) && !(fl & (F_YLO | F_YHI));
+        }
+        const uint32_t bal = __ballot_sync(0xffffffffu, nearc);
+        if (!bal) continue;
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(a.near_count, (uint32_t)__popc(bal));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (nearc) a.near_list[base + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)(L.c_off + idx);
+    }
+}
+
+// Split sweep, step 3: one thread per listed near-obstacle cell (a
+// persistent grid over the list), the same update as the fused path.
+template <int PREC, int ODD, bool SINGLE>
+__global__ void __launch_bounds__(256, SweepBounds<PREC>::MINB) near_kernel(const __grid_constant__ SweepArgs a) {
+    pdl_enter();
+    using C = typename Store<PREC>::C;
+    __shared__ uint32_t tkey[256];
+    __shared__ typename Acc<PREC>::V tval[256][6];
+    tkey[threadIdx.x] = SLOT_EMPTY;
+    const uint32_t n = *a.near_count;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t cell = a.near_list[i];
+        int li = 0;
+        if (!SINGLE) {
+            int lo = 0, hi = a.nlat - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (a.lat[mid].c_off <= (long long)cell) lo = mid; else hi = mid - 1;
+            }
+            li = lo;
+        }
+        const LatDev &L = SINGLE ? a.lat0 : a.lat[li];
+        const int idx = (int)((long long)cell - L.c_off);
+        C g[Q];
+        near_cell<PREC, ODD, 0>(a, L, li, idx, &tkey[threadIdx.x], tval[threadIdx.x], nullptr, g);
+    }
+    flush_forces<PREC>(a, tkey, tval);
+}
+
 template <int PREC, int ODD, bool SINGLE>
 cudaError_t launch_one(int variant, const SweepArgs &a, int grid, int block, cudaStream_t s) {
     if (variant == SWEEP_STAGED) {
@@ -1096,6 +1156,20 @@ cudaError_t launch_one(int variant, const SweepArgs &a, int grid, int block, cud
             attr = true;
         }
         return launch_pdl(sweep_ring<PREC, ODD, SINGLE>, grid, RingCfg<PREC>::TILE, smem, s, a);
+    } else if (a.near_list) {
+        static int wave = 0;  // resident blocks of the near kernel on all SMs (host-side, per instantiation)
+        if (!wave) {
+            int dev = 0, sms = 0, nb = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, near_kernel<PREC, ODD, SINGLE>, 128, 0);
+            wave = (sms > 0 ? sms : 1) * (nb > 0 ? nb : 1);
+        }
+        cudaError_t e = cudaMemsetAsync(a.near_count, 0, sizeof(uint32_t), s);
+        if (e == cudaSuccess) e = launch_pdl(near_list_kernel<SINGLE>, wave, 256, 0, s, a, block);
+        if (e == cudaSuccess) e = launch_pdl(sweep_kernel<PREC, ODD, SINGLE>, grid, block, 0, s, a);
+        if (e == cudaSuccess) e = launch_pdl(near_kernel<PREC, ODD, SINGLE>, wave, 128, 0, s, a);
+        return e;
     } else {
         return launch_pdl(sweep_kernel<PREC, ODD, SINGLE>, grid, block, 0, s, a);
     }

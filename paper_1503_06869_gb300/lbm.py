@@ -52,7 +52,7 @@ class lbm_info(C.Structure):
     _fields_ = [("ncells_total", C.c_longlong), ("nfluid_hint", C.c_longlong),
                 ("nlattices", C.c_int), ("nparticles", C.c_int), ("steps_done", C.c_longlong),
                 ("device_bytes", C.c_size_t), ("sweep_grid", C.c_int), ("sweep_block", C.c_int),
-                ("bytes_per_population", C.c_int)]
+                ("bytes_per_population", C.c_int), ("sweep_split", C.c_int)]
 
 
 # name -> (restype, argtypes) for every entry point of include/lbm.h
@@ -77,6 +77,7 @@ SIGNATURES = {
     "lbm_set_launch": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "lbm_autotune": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "lbm_set_graphs": (C.c_int, [C.c_void_p, C.c_int]),
+    "lbm_set_sweep_split": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_set_sweep_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_get_sweep_timing": (C.c_int, [C.c_void_p, C.POINTER(C.c_double),
                                        C.POINTER(C.c_longlong)]),
@@ -228,6 +229,10 @@ def lbm_autotune(ctx):
     b, g = C.c_int(0), C.c_int(0)
     _check(load().lbm_autotune(ctx, C.byref(b), C.byref(g)), ctx)
     return b.value, g.value
+
+
+def lbm_set_sweep_split(ctx, enable: bool):
+    _check(load().lbm_set_sweep_split(ctx, 1 if enable else 0), ctx)
 
 
 def lbm_set_graphs(ctx, enable: bool):
