@@ -157,26 +157,51 @@ __device__ __forceinline__ int tile_lattice(const SweepArgs &a, int tile) {
 // FP64 chain on the sweep's critical path stalls the whole sweep, so the
 // partials are compensated FP32 sums (about 48 significant bits) and only the
 // global accumulators are FP64.
+// float -> double by bit manipulation (exact for every float): GB300 issues
+// the conversion instruction on its FP64 pipe, integer operations are free.
+__device__ __forceinline__ double f2d_exact(float f) {
+    const uint32_t u = __float_as_uint(f);
+    const uint64_t sign = (uint64_t)(u >> 31) << 63;
+    const uint32_t e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
+    uint64_t bits;
+    if (e == 0xFFu) {
+        bits = sign | (0x7FFull << 52) | ((uint64_t)m << 29);
+    } else if (e != 0) {
+        bits = sign | ((uint64_t)(e + 896u) << 52) | ((uint64_t)m << 29);
+    } else if (m == 0) {
+        bits = sign;
+    } else {  // subnormal: m 2^-149 with the leading one of m at bit p
+        const int p = 31 - __clz((int)m);
+        bits = sign | ((uint64_t)(p + 874) << 52) | ((uint64_t)((m << (23 - p)) & 0x7FFFFFu) << 29);
+    }
+    return __longlong_as_double((long long)bits);
+}
+
 template <int PREC> struct Acc {
     using V = df;
+    // add to an FP64 accumulator: the two parts as two exact FP64 atomics
+    // (the additions happen in the L2, not on the SM's FP64 pipe)
+    static __device__ __forceinline__ void atomic_add(double *g, V x) {
+        atomicAdd(g, f2d_exact(x.hi));
+        if (x.lo != 0.f) atomicAdd(g, f2d_exact(x.lo));
+    }
     static __device__ __forceinline__ V zero() { return {0.f, 0.f}; }
     static __device__ __forceinline__ V add(V x, V y) { return df_add(x, y); }
     static __device__ __forceinline__ V sub(V x, V y) { return df_add(x, df_neg(y)); }
     static __device__ __forceinline__ V mul(V x, V y) { return df_mul(x, y); }
     static __device__ __forceinline__ V from(double x) { return df_from_double(x); }
-    static __device__ __forceinline__ double to_double(V x) { return df_to_double(x); }
     static __device__ __forceinline__ V shfl_xor(V x, int o) {
         return {__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o)};
     }
 };
 template <> struct Acc<LBM_F64> {
     using V = double;
+    static __device__ __forceinline__ void atomic_add(double *g, V x) { atomicAdd(g, x); }
     static __device__ __forceinline__ V zero() { return 0.0; }
     static __device__ __forceinline__ V add(V x, V y) { return x + y; }
     static __device__ __forceinline__ V sub(V x, V y) { return x - y; }
     static __device__ __forceinline__ V mul(V x, V y) { return x * y; }
     static __device__ __forceinline__ V from(double x) { return x; }
-    static __device__ __forceinline__ double to_double(V x) { return x; }
     static __device__ __forceinline__ V shfl_xor(V x, int o) { return __shfl_xor_sync(0xffffffffu, x, o); }
 };
 
@@ -191,7 +216,7 @@ __device__ __forceinline__ void tacc_add(const SweepArgs &a, uint32_t *tkey, typ
         if (*tkey != SLOT_EMPTY) {
             double *g = global_acc(a, *tkey);
             const int nk = (*tkey & KEY_WALL) ? 3 : 6;
-            for (int k = 0; k < nk; ++k) atomicAdd(g + k, A::to_double(tval[k]));
+            for (int k = 0; k < nk; ++k) A::atomic_add(g + k, tval[k]);
         }
         *tkey = key;
         for (int k = 0; k < 6; ++k) tval[k] = A::zero();
@@ -662,7 +687,7 @@ __device__ __forceinline__ void flush_forces(const SweepArgs &a, uint32_t *tkey,
             typename A::V v = mine ? tval[threadIdx.x][k] : A::zero();
 #pragma unroll
             for (int o = 16; o; o >>= 1) v = A::add(v, A::shfl_xor(v, o));
-            if (lane == leader) atomicAdd(g + k, A::to_double(v));
+            if (lane == leader) A::atomic_add(g + k, v);
         }
         if (mine) key = SLOT_EMPTY;
     }
@@ -1077,32 +1102,37 @@ __global__ void __launch_bounds__(256, SweepBounds<PREC>::MINB)
 // (bulk-copy pipeline), SWEEP_RING (per-thread cp.async prefetch ring).
 // Split sweep, step 1: the near-obstacle cells (F_NEAR without a flat-wall
 // flag) of the tiles marked in the tile bits, compacted into a.near_list --
-// one warp per 32 cells of a tile, one atomic per warp.  T = cells per tile.
+// one block per tile (blockDim = cells per tile), one atomic per tile.
 template <bool SINGLE>
-__global__ void near_list_kernel(const __grid_constant__ SweepArgs a, int T) {
+__global__ void __launch_bounds__(256) near_list_kernel(const __grid_constant__ SweepArgs a) {
     pdl_enter();
-    const int lane = threadIdx.x & 31;
-    const long long wpb = blockDim.x >> 5;
-    const long long chunks = T >> 5;
-    const long long total = (long long)a.ntiles * chunks;
-    for (long long w = blockIdx.x * wpb + (threadIdx.x >> 5); w < total; w += (long long)gridDim.x * wpb) {
-        const int tile = (int)(w / chunks), ch = (int)(w - (long long)tile * chunks);
-        if (a.tbits && !((a.tbits[tile >> 5] >> (tile & 31)) & 1u)) continue;  // uniform per warp
-        const int li = tile_lattice<SINGLE>(a, tile);
-        const LatDev &L = SINGLE ? a.lat0 : a.lat[li];
-        const int idx = (tile - L.tile0) * T + ch * 32 + lane;
-        bool nearc = false;
-        if (idx < L.n) {
-            const uint8_t fl = a.flags[L.c_off + idx];
-            nearc = (fl & F_NEAR) && !(fl & (F_YLO | F_YHI));
-        }
-        const uint32_t bal = __ballot_sync(0xffffffffu, nearc);
-        if (!bal) continue;
-        uint32_t base = 0;
-        if (lane == 0) base = atomicAdd(a.near_count, (uint32_t)__popc(bal));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (nearc) a.near_list[base + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)(L.c_off + idx);
+    const int tile = blockIdx.x;
+    if (a.tbits && !((a.tbits[tile >> 5] >> (tile & 31)) & 1u)) return;  // uniform per block
+    const int li = tile_lattice<SINGLE>(a, tile);
+    const LatDev &L = SINGLE ? a.lat0 : a.lat[li];
+    const int idx = (tile - L.tile0) * blockDim.x + threadIdx.x;
+    bool nearc = false;
+    if (idx < L.n) {
+        const uint8_t fl = a.flags[L.c_off + idx];
+        nearc = (fl & F_NEAR) && !(fl & (F_YLO | F_YHI));
     }
+    __shared__ uint32_t wcount[8];
+    __shared__ uint32_t base;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t bal = __ballot_sync(0xffffffffu, nearc);
+    if (lane == 0) wcount[warp] = (uint32_t)__popc(bal);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t sum = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            const uint32_t c = wcount[w];
+            wcount[w] = sum;
+            sum += c;
+        }
+        base = sum ? atomicAdd(a.near_count, sum) : 0u;
+    }
+    __syncthreads();
+    if (nearc) a.near_list[base + wcount[warp] + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)(L.c_off + idx);
 }
 
 // Split sweep, step 3: one thread per listed near-obstacle cell (a
@@ -1166,7 +1196,7 @@ cudaError_t launch_one(int variant, const SweepArgs &a, int grid, int block, cud
             wave = (sms > 0 ? sms : 1) * (nb > 0 ? nb : 1);
         }
         cudaError_t e = cudaMemsetAsync(a.near_count, 0, sizeof(uint32_t), s);
-        if (e == cudaSuccess) e = launch_pdl(near_list_kernel<SINGLE>, wave, 256, 0, s, a, block);
+        if (e == cudaSuccess) e = launch_pdl(near_list_kernel<SINGLE>, a.ntiles, block, 0, s, a);
         if (e == cudaSuccess) e = launch_pdl(sweep_kernel<PREC, ODD, SINGLE>, grid, block, 0, s, a);
         if (e == cudaSuccess) e = launch_pdl(near_kernel<PREC, ODD, SINGLE>, wave, 128, 0, s, a);
         return e;
