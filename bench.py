@@ -29,7 +29,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from lbm_inputs import large_shear, small_shear, batched_shear, fibre_suspension  # noqa: E402
+from lbm_inputs import large_shear, small_shear, batched_shear, fibre_suspension, Particle  # noqa: E402
 
 BYTES_PER_POP = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
 
@@ -219,6 +219,38 @@ def config_of(w, args, nfluid):
     return cfg
 
 
+def run_sequential(args, w, rank, world):
+    """The lattices of a batch as independent contexts, each step launched
+    lattice by lattice (the baseline the single batched launch replaces)."""
+    import torch
+    from paper_1503_06869_gb300 import lbm
+    torch.cuda.set_device(0)
+    sims = []
+    for c, lat in enumerate(w.lattices):
+        parts = [Particle(**{**p.__dict__, "cell": 0}) for p in w.particles if p.cell == c]
+        sims.append(lbm.Simulation([lat], parts, prec=args.prec))
+    for _ in range(args.warmup):
+        for s in sims:
+            s.step(1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for s in sims:
+            s.step(1)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    value = w.ncells * args.steps / el / 1e6
+    line = {"metric": "MLUPS", "value": round(value, 1), "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(el * 1e3 / args.steps, 5), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
+            "config": {**config_of(w, args, 0), "mode": "sequential single-lattice contexts"}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for s in sims:
+        s.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -226,6 +258,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large", choices=["large", "small", "batched", "fibre"])
+    ap.add_argument("--sequential", action="store_true",
+                    help="batched workload: one context per lattice, stepped one after another")
     ap.add_argument("--closure", action="store_true",
                     help="enable the learned force/torque closure (seeded small parameters)")
     ap.add_argument("--prec", default="f32", choices=["f64", "f32", "f16", "bf16"])
@@ -236,6 +270,8 @@ def main():
     w = workload(args.workload)
     if args.impl == "reference":
         return run_reference(args, w, rank, world)
+    if args.sequential:
+        return run_sequential(args, w, rank, world)
 
     import torch
     from paper_1503_06869_gb300 import lbm
