@@ -133,13 +133,15 @@ class ClockSampler:
 
 
 def dist_setup(n_gpus: int):
+    """One process per GPU under torchrun: NCCL when CUDA is present, else
+    gloo (host-side runs of the replica logic)."""
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
+        import torch
         import torch.distributed as dist
-        backend = "nccl"
-        dist.init_process_group(backend=backend)
+        dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
     return rank, world, local
 
 
@@ -154,9 +156,16 @@ def max_over_ranks(x: float, world: int) -> float:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, ms_max: float) -> float:
+    """Whole-job throughput of N replicas (weak scaling): the units every rank
+    processed, over the slowest rank's time, in millions per second."""
+    return units_per_rank * world / (ms_max * 1e-3) / 1e6
 
 
 def cpu_baseline(w, budget_s: float = 12.0, threads: int | None = None):
@@ -318,7 +327,7 @@ def main():
     lbm.lbm_set_sweep_timing(h, False)
     ms_max = max_over_ranks(ms, world)
     cells = w.ncells
-    value = cells * args.steps * world / (ms_max * 1e-3) / 1e6
+    value = whole_job_rate(cells * args.steps, world, ms_max)
 
     # roofline of the sweep kernel (dominant kernel): algorithmic bytes =
     # 19 loads + 19 stores per fluid cell update
