@@ -225,3 +225,17 @@ def test_closure_is_off_without_moving_walls(env):
     finally:
         a.close()
         b.close()
+
+
+def test_training_driver_end_to_end_small(env):
+    # the paired coarse/fine data pipeline, training and evaluation at toy sizes
+    L, _ = env
+    from paper_1503_06869_gb300 import closure_train as ct
+    X, Y, C, Fn = ct.make_samples(3, coarse_box=(24, 20, 24), a=5.0, b=1.5, uw=0.02, coarse_steps=20, scale=2,
+                                  log=lambda s: None)
+    assert X.shape == (3, cl.N_IN) and Y.shape == (3, 6) and np.isfinite(X).all() and np.isfinite(Y).all()
+    np.testing.assert_allclose(Y, Fn - C)
+    p32, p16, hist = ct.train(X[:2], Y[:2], steps=50, lr=1e-3)
+    assert hist[-1] <= hist[0] and np.isfinite(p32).all()
+    res = ct.evaluate(C[2:], Fn[2:], ct.predict(p32, X[2:]))
+    assert all(np.isfinite(v) for v in res.values())
