@@ -27,6 +27,7 @@ PID_FLUID = 0xFFFFFFFF
 PID_WALL_YLO = 0xFFFFFFFE
 PID_WALL_YHI = 0xFFFFFFFD
 PID_WALL = 0xFFFFFFFC
+SHAPE_ELLIPSOID, SHAPE_SPHEROCYLINDER = 0, 1
 
 
 class SplitMix64:
@@ -101,7 +102,9 @@ class Lattice:
 
 @dataclass
 class Particle:
-    """Rigid ellipsoid: centre, orientation, velocities, semi-axes (body x,y,z)."""
+    """Rigid body: centre, orientation, velocities, semi-axes (body x,y,z).
+    shape 0: ellipsoid with those semi-axes; shape 1: spherocylinder of total
+    length L and radius r along body x, semi_axes = (L/2, r, r)."""
     pos: Tuple[float, float, float]
     quat: Tuple[float, float, float, float]
     semi_axes: Tuple[float, float, float]
@@ -112,6 +115,7 @@ class Particle:
     ext_torque: Tuple[float, float, float] = (0.0, 0.0, 0.0)
     cell: int = 0
     fixed: int = 0
+    shape: int = 0
 
 
 @dataclass

@@ -22,7 +22,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 BUILD = os.path.join(HERE, "_build")
 SRC = os.path.join(HERE, "lbm_oracle.c")
 HDR = os.path.join(HERE, "lbm_oracle.h")
-PSTRIDE = 25
+PSTRIDE = 26
+SHAPE_ELLIPSOID, SHAPE_SPHEROCYLINDER = 0, 1
 Q = 19
 
 _lock = threading.Lock()
@@ -97,7 +98,7 @@ def _ptr(a: np.ndarray):
 
 def particle_records(particles) -> np.ndarray:
     """Pack particle objects (pos, quat, vel, omega, semi_axes, density,
-    ext_force, ext_torque, fixed, cell) into the oracle's record array."""
+    ext_force, ext_torque, fixed, cell, shape) into the oracle's record array."""
     out = np.zeros((len(particles), PSTRIDE), dtype=np.float64)
     for i, p in enumerate(particles):
         out[i, 0:3] = p.pos
@@ -110,6 +111,7 @@ def particle_records(particles) -> np.ndarray:
         out[i, 20:23] = p.ext_torque
         out[i, 23] = float(p.fixed)
         out[i, 24] = float(p.cell)
+        out[i, 25] = float(getattr(p, "shape", SHAPE_ELLIPSOID))
     return out
 
 

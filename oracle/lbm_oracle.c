@@ -175,7 +175,11 @@ static double min_image(double d, int n, int periodic) {
 }
 
 /* Obstacle mapping of Sec. 4.2: cell (i,j,k) is covered iff its centre lies
-   inside the ellipsoid (p0/a)^2 + (p1/b)^2 + (p2/c)^2 <= 1 with p = R^T d. */
+   inside the body, with p = R^T d the centre in the body frame:
+   ellipsoid: (p0/a)^2 + (p1/b)^2 + (p2/c)^2 <= 1;
+   spherocylinder of radius r and half length L/2 = a along body x: the
+   distance from p to the axis segment |p0| <= a - r is at most r, i.e.
+   t^2 + p1^2 + p2^2 <= r^2 with t = max(|p0| - (a - r), 0). */
 int orc_inside(const double *rec, int nx, int ny, int nz, const int periodic[3], int i, int j,
                int k) {
     double d0 = min_image((double)i - rec[0], nx, periodic[0]);
@@ -186,12 +190,38 @@ int orc_inside(const double *rec, int nx, int ny, int nz, const int periodic[3],
     double p0 = R[0] * d0 + R[3] * d1 + R[6] * d2;
     double p1 = R[1] * d0 + R[4] * d1 + R[7] * d2;
     double p2 = R[2] * d0 + R[5] * d1 + R[8] * d2;
+    if (rec[25] == ORC_SHAPE_SPHEROCYLINDER) {
+        double r = rec[14];
+        double t = fabs(p0) - (rec[13] - r);
+        if (t < 0.0) t = 0.0;
+        double s = t * t + p1 * p1 + p2 * p2;
+        return s <= r * r;
+    }
     double t0 = p0 / rec[13], t1 = p1 / rec[14], t2 = p2 / rec[15];
     double s = t0 * t0 + t1 * t1 + t2 * t2;
     return s <= 1.0;
 }
 
+/* Mass and principal moments of inertia of a homogeneous body of density
+   rec[16].  Spherocylinder: a cylinder of length 2h = L - 2r (mass m_c) and
+   two hemispherical caps forming a sphere of radius r (mass m_s).  About the
+   axis: m_c r^2/2 + 2 m_s r^2/5.  About a transverse axis through the
+   centre: the cylinder's m_c (r^2/4 + (2h)^2/12), and for each cap (mass
+   m_s/2, centroid 3r/8 from its flat face, which lies h from the centre) its
+   moment about the face, m_s r^2/5, moved to the centroid and then to the
+   centre by the parallel-axis theorem: in total m_s (2r^2/5 + h^2 + 3hr/4). */
 void orc_particle_mass_inertia(const double *rec, double *mass, double inertia[3]) {
+    if (rec[25] == ORC_SHAPE_SPHEROCYLINDER) {
+        double r = rec[14], h = rec[13] - rec[14];
+        double mc = rec[16] * M_PI * r * r * (2.0 * h);
+        double ms = rec[16] * (4.0 / 3.0) * M_PI * r * r * r;
+        *mass = mc + ms;
+        inertia[0] = mc * r * r / 2.0 + 2.0 * ms * r * r / 5.0;
+        inertia[1] = mc * (r * r / 4.0 + (2.0 * h) * (2.0 * h) / 12.0) +
+                     ms * (2.0 * r * r / 5.0 + h * h + 3.0 * h * r / 4.0);
+        inertia[2] = inertia[1];
+        return;
+    }
     double a = rec[13], b = rec[14], c = rec[15];
     double m = rec[16] * (4.0 / 3.0) * M_PI * a * b * c;
     *mass = m;

@@ -24,8 +24,13 @@ extern "C" {
 #endif
 
 /* doubles per particle record: pos3 quat4(w,x,y,z) vel3 omega3 semi3 density
-   extF3 extM3 fixed(0/1) cell(ignored by the oracle) */
-#define ORC_PSTRIDE 25
+   extF3 extM3 fixed(0/1) cell(ignored by the oracle) shape.
+   shape 0: ellipsoid with semi-axes (a, b, c) along body x, y, z;
+   shape 1: spherocylinder (Sec. 5.1, Fig. Capsule) of total length L and
+   radius r along body x, given as semi = (L/2, r, r). */
+#define ORC_PSTRIDE 26
+#define ORC_SHAPE_ELLIPSOID 0
+#define ORC_SHAPE_SPHEROCYLINDER 1
 
 #define ORC_PID_FLUID    0xFFFFFFFFu
 #define ORC_PID_WALL_YLO 0xFFFFFFFEu
