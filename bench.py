@@ -274,6 +274,8 @@ def main():
     ap.add_argument("--prec", default="f32", choices=["f64", "f32", "f16", "bf16"])
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--remap-separate", action="store_true",
+                    help="run the re-mapping step as five launches instead of one cooperative launch")
     args = ap.parse_args()
     rank, world, local = dist_setup(args.gpus)
     w = workload(args.workload)
@@ -291,6 +293,8 @@ def main():
         # throughput only: the parameters are seeded and small, not trained
         theta = np.random.default_rng(0).normal(size=lbm.CLOSURE_PARAMS) * 0.01
         lbm.lbm_set_closure(h, theta.astype(np.float16))
+    if args.remap_separate:
+        lbm.lbm_set_remap_fused(h, False)
     lbm.lbm_autotune(h)
     info = lbm.lbm_get_info(h)
     sim.step(args.warmup)
@@ -378,7 +382,8 @@ def main():
                     "h2d_bytes_per_step": 24 * len(w.particles),
                     "d2h_bytes_per_step": 48 * len(w.particles)},
             "gpu_launches": int(launches),
-            "launch": {"block": info.sweep_block, "grid": info.sweep_grid, "split": bool(info.sweep_split)},
+            "launch": {"block": info.sweep_block, "grid": info.sweep_grid, "split": bool(info.sweep_split),
+                       "remap_fused": bool(info.remap_fused), "remap_grid": info.remap_grid},
             "clocks": clk}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)

@@ -102,13 +102,19 @@ typedef struct lbm_grid_desc {
     void *user;                /* passed to dev_alloc / dev_free */
 } lbm_grid_desc;
 
-/* One rigid ellipsoid (Sec. 4.2-4.3).  Semi-axes are along the body x, y, z
- * axes; quat = (w, x, y, z) rotates body to world coordinates and is
- * normalised by the library.  Mass = density * 4/3 pi a b c (density relative
- * to rho0 = 1 units), inertia of the solid ellipsoid.  ext_force and
- * ext_torque are added to the hydrodynamic force and torque every step.  A
- * fixed body keeps its pose and velocities.  cell selects the lattice of a
- * batch (0 for a single lattice). */
+/* One rigid body (Sec. 4.2-4.3).  shape LBM_SHAPE_ELLIPSOID: semi-axes
+ * (a, b, c) along the body x, y, z axes, mass = density * 4/3 pi a b c.
+ * shape LBM_SHAPE_SPHEROCYLINDER (the particles of Sec. 5.1, Fig. Capsule): a
+ * cylinder of radius r with hemispherical end caps, total length L along body
+ * x, given as semi_axes = (L/2, r, r) with L/2 >= r; mass = density *
+ * (pi r^2 (L - 2r) + 4/3 pi r^3).  Inertia of the homogeneous solid.  quat =
+ * (w, x, y, z) rotates body to world coordinates and is normalised by the
+ * library; density is relative to rho0 = 1 units.  ext_force and ext_torque
+ * are added to the hydrodynamic force and torque every step.  A fixed body
+ * keeps its pose and velocities.  cell selects the lattice of a batch (0 for
+ * a single lattice). */
+#define LBM_SHAPE_ELLIPSOID 0
+#define LBM_SHAPE_SPHEROCYLINDER 1
 typedef struct lbm_particle {
     double pos[3];
     double quat[4];
@@ -120,6 +126,7 @@ typedef struct lbm_particle {
     double ext_torque[3];
     int cell;
     int fixed;
+    int shape;                 /* LBM_SHAPE_* */
 } lbm_particle;
 
 /* Create one lattice, fluid at rest with density rho0 (f_q = w_q rho0).
@@ -226,6 +233,8 @@ typedef struct lbm_info {
     int sweep_grid, sweep_block;/* launch shape of the sweep kernel */
     int bytes_per_population;   /* 8, 4 or 2 */
     int sweep_split;            /* 1: the direct sweep runs split (lbm_set_sweep_split) */
+    int remap_fused;            /* 1: the re-mapping step runs as one cooperative launch */
+    int remap_grid;             /* blocks of that launch (0 when not fused) */
 } lbm_info;
 
 lbm_status lbm_get_info(lbm_ctx *ctx, lbm_info *info);
@@ -250,6 +259,18 @@ lbm_status lbm_set_launch(lbm_ctx *ctx, int block, int grid);
  * suspensions); the autotuner decides.  Applies to the direct sweep only;
  * takes effect at the next lbm_step. */
 lbm_status lbm_set_sweep_split(lbm_ctx *ctx, int enable);
+
+/* Fused re-mapping step (enable != 0, the default): the rigid-body update
+ * (Sec. 4.3) and the four passes of the obstacle re-mapping (Sec. 4.2:
+ * uncover, claim, refill/fix-up, flags) run as one cooperative launch of at
+ * most one resident wave, with grid-wide barriers between the passes, instead
+ * of five launches.  Used only where the device and driver accept cooperative
+ * launches (probed once per context, eagerly and inside a captured graph);
+ * otherwise, or with enable = 0, the separate kernels run.  Results are
+ * identical either way.  A barrier wait that runs out (it cannot while the
+ * launch is resident) makes lbm_step return LBM_ERR_TIMEOUT.  Takes effect at
+ * the next lbm_step. */
+lbm_status lbm_set_remap_fused(lbm_ctx *ctx, int enable);
 
 /* Choose the sweep launch shape by timing candidates on this context (runs
  * sweeps on scratch copies: the state is restored afterwards).  The chosen

@@ -50,6 +50,8 @@ struct lbm_ctx {
     int np = 0;
     PartDev P{};
     std::vector<void *> part_bufs;
+    std::vector<int> shape_h;       // per body: LBM_SHAPE_*
+    std::vector<double> density_h;  // per body: density as given
 
     void *f_arena = nullptr;        // population allocation: guard | planes | guard
     long long guard = 0;            // guard band in elements on each side
@@ -58,10 +60,18 @@ struct lbm_ctx {
     int variant = SWEEP_DIRECT;     // sweep kernel variant
     int block = 128, grid = 0, ntiles = 0;
     int remap_bpb = 8;
+    // fused re-mapping step: launch form found by the probe (-1 not probed,
+    // 0 unavailable, 1 cooperative, 2 cooperative + programmatic dependency),
+    // user switch, grid and barrier state
+    int remap_mode = -1;
+    bool remap_fused = true;
+    int remap_grid = 0;
+    GridBar *gbar = nullptr;
 
     bool graphs = true;
     cudaGraphExec_t gexec = nullptr;
     bool gvalid = false;
+    long long graph_launches = 0;   // kernels in one replay of the two-step graph
 
     bool timing = false;
     std::vector<cudaEvent_t> ev;
@@ -192,6 +202,10 @@ SweepArgs sweep_args(lbm_ctx *ctx) {
 // kernels one sweep issues (the split direct sweep: list, sweep, near cells)
 int sweep_kernels(const lbm_ctx *ctx) { return (ctx->split && ctx->variant == SWEEP_DIRECT) ? 3 : 1; }
 
+bool fused_remap(const lbm_ctx *ctx) {
+    return ctx->remap_fused && ctx->remap_mode > 0 && ctx->np > 0 && ctx->remap_grid > 0;
+}
+
 RemapArgs remap_args(lbm_ctx *ctx) {
     RemapArgs a;
     a.lat = ctx->lat_d;
@@ -228,8 +242,6 @@ MlpArgs closure_mlp_args(lbm_ctx *ctx) {
     m.n = ctx->np;
     return m;
 }
-
-int closure_kernels(const lbm_ctx *ctx) { return (ctx->closure && ctx->np > 0) ? 2 : 0; }
 
 // Recount the direct sweep's tile bits from the flags (clears stale marks).
 lbm_status recount_tiles(lbm_ctx *ctx) {
@@ -282,11 +294,17 @@ lbm_status enqueue_step(lbm_ctx *ctx, bool timed) {
         ctx->launches += 2;
     }
     RemapArgs ra = remap_args(ctx);
-    CK(launch_rigid_body(ra, ctx->stream));
-    ctx->launches += sweep_kernels(ctx) + 1;
-    if (ctx->np > 0) {
-        CK(launch_remap_step(ctx->prec, 1 - parity, ra, ctx->remap_bpb, ctx->stream));
-        ctx->launches += kernels_per_remap_step();
+    if (fused_remap(ctx)) {
+        CK(launch_remap_fused(ctx->prec, 1 - parity, ra, ctx->remap_bpb, ctx->remap_grid, ctx->remap_mode,
+                              ctx->gbar, ctx->stream));
+        ctx->launches += sweep_kernels(ctx) + 1;
+    } else {
+        CK(launch_rigid_body(ra, ctx->stream));
+        ctx->launches += sweep_kernels(ctx) + 1;
+        if (ctx->np > 0) {
+            CK(launch_remap_step(ctx->prec, 1 - parity, ra, ctx->remap_bpb, ctx->stream));
+            ctx->launches += kernels_per_remap_step();
+        }
     }
     ctx->t += 1;
     return LBM_OK;
@@ -313,6 +331,7 @@ lbm_status build_graph(lbm_ctx *ctx) {
     lbm_status s2 = s1 == LBM_OK ? enqueue_step(ctx, false) : s1;
     cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
     ctx->t = t0;
+    ctx->graph_launches = ctx->launches - l0;
     ctx->launches = l0;
     if (s2 != LBM_OK) {
         if (g) cudaGraphDestroy(g);
@@ -478,6 +497,7 @@ lbm_status create_common(const lbm_grid_desc *cells, int ncells, lbm_ctx **out) 
     ctx->wall_acc = (double *)owned_alloc(ctx, sizeof(double) * 6 * ACC_COPIES * ncells);
     ctx->wall_last = (double *)owned_alloc(ctx, sizeof(double) * 6 * ncells);
     ctx->err = (uint32_t *)owned_alloc(ctx, 16);
+    ctx->gbar = (GridBar *)owned_alloc(ctx, 16);
     {
         long long tiles32 = 0;  // tiles of the smallest direct-sweep tile (32 cells)
         for (auto &L : ctx->lat_h) tiles32 += (L.n + 31) / 32;
@@ -485,7 +505,7 @@ lbm_status create_common(const lbm_grid_desc *cells, int ncells, lbm_ctx **out) 
     }
     if (!ctx->lat_d || !ctx->f || !ctx->flags || !ctx->pid || !ctx->pid_prev || !ctx->wall_acc ||
         !ctx->wall_last || !ctx->err || !ctx->tbits || !ctx->links || !ctx->nbody || !ctx->near_list ||
-        !ctx->near_count) {
+        !ctx->near_count || !ctx->gbar) {
         lbm_destroy(ctx);
         return LBM_ERR_OOM;
     }
@@ -501,7 +521,8 @@ lbm_status create_common(const lbm_grid_desc *cells, int ncells, lbm_ctx **out) 
         cudaMemsetAsync(ctx->pid, 0xFF, (size_t)coff * 4, ctx->stream) != cudaSuccess ||
         cudaMemsetAsync(ctx->wall_acc, 0, sizeof(double) * 6 * ACC_COPIES * ncells, ctx->stream) != cudaSuccess ||
         cudaMemsetAsync(ctx->wall_last, 0, sizeof(double) * 6 * ncells, ctx->stream) != cudaSuccess ||
-        cudaMemsetAsync(ctx->err, 0, 16, ctx->stream) != cudaSuccess) {
+        cudaMemsetAsync(ctx->err, 0, 16, ctx->stream) != cudaSuccess ||
+        cudaMemsetAsync(ctx->gbar, 0, 16, ctx->stream) != cudaSuccess) {
         lbm_destroy(ctx);
         return LBM_ERR_CUDA;
     }
@@ -566,13 +587,19 @@ lbm_status lbm_set_particles(lbm_ctx *ctx, const lbm_particle *p, int n) {
     std::vector<double> pos(3 * n), quat(4 * n), vel(3 * n), om(3 * n), L(3 * n), semi(3 * n), mass(n),
         inertia(3 * n), extF(3 * n), extM(3 * n), minv(n), Iinv(3 * n), R64(9 * (size_t)n);
     std::vector<float> bodyf(BF_STRIDE * (size_t)n, 0.0f);
-    std::vector<int> cell(n), fixed(n), region(6 * n);
+    std::vector<int> cell(n), fixed(n), region(6 * n), shape(n);
+    std::vector<double> density(n);
     for (int i = 0; i < n; ++i) {
         const lbm_particle &b = p[i];
         if (b.cell < 0 || b.cell >= ctx->nlat) return fail(ctx, LBM_ERR_ARG, "particle cell index out of range");
         if (!(b.semi_axes[0] > 0 && b.semi_axes[1] > 0 && b.semi_axes[2] > 0))
             return fail(ctx, LBM_ERR_ARG, "semi-axes must be positive");
         if (!(b.density > 0)) return fail(ctx, LBM_ERR_ARG, "density must be positive");
+        if (b.shape != LBM_SHAPE_ELLIPSOID && b.shape != LBM_SHAPE_SPHEROCYLINDER)
+            return fail(ctx, LBM_ERR_ARG, "unknown particle shape");
+        const bool capsule = b.shape == LBM_SHAPE_SPHEROCYLINDER;
+        if (capsule && !(b.semi_axes[1] == b.semi_axes[2] && b.semi_axes[0] >= b.semi_axes[1]))
+            return fail(ctx, LBM_ERR_ARG, "spherocylinder needs semi_axes = (L/2, r, r) with L/2 >= r");
         double q[4] = {b.quat[0], b.quat[1], b.quat[2], b.quat[3]};
         const double nrm = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
         if (!(nrm > 0) || !std::isfinite(nrm)) return fail(ctx, LBM_ERR_ARG, "quaternion must be non-zero");
@@ -584,9 +611,12 @@ lbm_status lbm_set_particles(lbm_ctx *ctx, const lbm_particle *p, int n) {
         for (int a = 0; a < 3; ++a) {
             if (!std::isfinite(b.pos[a]) || !std::isfinite(b.vel[a]) || !std::isfinite(b.omega[a]))
                 return fail(ctx, LBM_ERR_ARG, "non-finite particle state");
-            const double e0 = R[3 * a] * b.semi_axes[0], e1 = R[3 * a + 1] * b.semi_axes[1],
-                         e2 = R[3 * a + 2] * b.semi_axes[2];
-            const double h = std::sqrt(e0 * e0 + e1 * e1 + e2 * e2);
+            // half extent along a: ellipsoid sqrt(sum_j (R_aj s_j)^2),
+            // spherocylinder |R_a0| (L/2 - r) + r
+            const double s0 = capsule ? b.semi_axes[1] : b.semi_axes[0];
+            const double e0 = R[3 * a] * s0, e1 = R[3 * a + 1] * b.semi_axes[1], e2 = R[3 * a + 2] * b.semi_axes[2];
+            const double h = std::sqrt(e0 * e0 + e1 * e1 + e2 * e2) +
+                             (capsule ? std::fabs(R[3 * a]) * (b.semi_axes[0] - b.semi_axes[1]) : 0.0);
             if (!per[a] && (b.pos[a] - h < 1.0 || b.pos[a] + h > dims[a] - 2.0))
                 return fail(ctx, LBM_ERR_ARG, "particle not inside the fluid region");
             if (per[a] && !(b.pos[a] >= 0.0 && b.pos[a] < dims[a]))
@@ -601,9 +631,25 @@ lbm_status lbm_set_particles(lbm_ctx *ctx, const lbm_particle *p, int n) {
             region[6 * i + a] = lo;
             region[6 * i + 3 + a] = hi - lo + 1;
         }
-        const double A = b.semi_axes[0], B = b.semi_axes[1], Cc = b.semi_axes[2];
-        const double m = b.density * (4.0 / 3.0) * M_PI * A * B * Cc;
-        const double I[3] = {m * (B * B + Cc * Cc) / 5.0, m * (A * A + Cc * Cc) / 5.0, m * (A * A + B * B) / 5.0};
+        double m, I[3];
+        if (capsule) {
+            // cylinder of length 2h (mass mc) and a sphere of radius r split
+            // into the two end caps (mass ms); transverse moment of the caps by
+            // the parallel-axis theorem (cap centroid 3r/8 from its flat face)
+            const double r = b.semi_axes[1], h = b.semi_axes[0] - b.semi_axes[1];
+            const double mc = b.density * M_PI * r * r * (2.0 * h);
+            const double ms = b.density * (4.0 / 3.0) * M_PI * r * r * r;
+            m = mc + ms;
+            I[0] = mc * r * r / 2.0 + 2.0 * ms * r * r / 5.0;
+            I[1] = mc * (r * r / 4.0 + (2.0 * h) * (2.0 * h) / 12.0) + ms * (2.0 * r * r / 5.0 + h * h + 3.0 * h * r / 4.0);
+            I[2] = I[1];
+        } else {
+            const double A = b.semi_axes[0], B = b.semi_axes[1], Cc = b.semi_axes[2];
+            m = b.density * (4.0 / 3.0) * M_PI * A * B * Cc;
+            I[0] = m * (B * B + Cc * Cc) / 5.0;
+            I[1] = m * (A * A + Cc * Cc) / 5.0;
+            I[2] = m * (A * A + B * B) / 5.0;
+        }
         // angular momentum L = R I R^T omega
         double ob[3], Lw[3];
         for (int a = 0; a < 3; ++a)
@@ -626,8 +672,10 @@ lbm_status lbm_set_particles(lbm_ctx *ctx, const lbm_particle *p, int n) {
         for (int k = 0; k < 9; ++k) R64[9 * (size_t)i + k] = R[k];
         float *bf = &bodyf[BF_STRIDE * (size_t)i];
         for (int k = 0; k < 9; ++k) bf[BF_R + k] = (float)R[k];
+        bf[BF_SHAPE] = capsule ? 1.0f : 0.0f;
+        bf[BF_CAPH] = capsule ? (float)((b.semi_axes[0] - b.semi_axes[1]) / b.semi_axes[1]) : 0.0f;
         for (int a = 0; a < 3; ++a) {
-            bf[BF_INV + a] = (float)(1.0 / b.semi_axes[a]);
+            bf[BF_INV + a] = (float)(1.0 / (capsule ? b.semi_axes[1] : b.semi_axes[a]));
             bf[BF_POS + a] = (float)b.pos[a];
             bf[BF_POSLO + a] = (float)(b.pos[a] - (double)bf[BF_POS + a]);
             bf[BF_U + a] = (float)b.vel[a];
@@ -635,6 +683,8 @@ lbm_status lbm_set_particles(lbm_ctx *ctx, const lbm_particle *p, int n) {
         }
         cell[i] = b.cell;
         fixed[i] = b.fixed ? 1 : 0;
+        shape[i] = b.shape;
+        density[i] = b.density;
     }
     // re-mapping launch shape: about four box cells per thread for the
     // largest body, at most ~64 blocks per SM over all bodies
@@ -652,6 +702,11 @@ lbm_status lbm_set_particles(lbm_ctx *ctx, const lbm_particle *p, int n) {
         const long long cap = (long long)(sms > 0 ? sms : 1) * 64;
         if (n > 0 && bpb * n > cap) bpb = cap / n > 0 ? cap / n : 1;
         ctx->remap_bpb = (int)bpb;
+        // fused step: one resident wave at most, no more blocks than units
+        if (n > 0 && ctx->remap_mode < 0) ctx->remap_mode = remap_fused_probe();
+        const long long units = bpb * n;
+        const long long wave = ctx->remap_mode > 0 ? remap_fused_max_blocks() : 0;
+        ctx->remap_grid = (int)(units < wave ? units : wave);
     }
     CK(cudaStreamSynchronize(ctx->stream));
     drop_graph(ctx);
@@ -689,6 +744,8 @@ lbm_status lbm_set_particles(lbm_ctx *ctx, const lbm_particle *p, int n) {
             return fail(ctx, LBM_ERR_OOM, "particle buffers");
         }
     ctx->np = n;
+    ctx->shape_h = shape;
+    ctx->density_h = density;
     auto up = [&](void *dst, const void *src, size_t bytes) -> cudaError_t {
         if (bytes == 0) return cudaSuccess;
         return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream);
@@ -754,12 +811,10 @@ lbm_status lbm_step(lbm_ctx *ctx, int nsteps) {
                 lbm_status s = build_graph(ctx);
                 if (s != LBM_OK) return s;
             }
-            const int per =
-                2 * (sweep_kernels(ctx) + 1 + closure_kernels(ctx) + (ctx->np > 0 ? kernels_per_remap_step() : 0));
             while (left >= 2) {
                 CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
                 ctx->t += 2;
-                ctx->launches += per;
+                ctx->launches += ctx->graph_launches;
                 left -= 2;
                 lbm_status s = maybe_recount();
                 if (s != LBM_OK) return s;
@@ -834,9 +889,10 @@ lbm_status lbm_get_particles(lbm_ctx *ctx, lbm_particle *p, int n) {
             b.ext_torque[a] = eM[3 * i + a];
         }
         for (int k = 0; k < 4; ++k) b.quat[k] = quat[4 * i + k];
-        b.density = mass[i] / ((4.0 / 3.0) * M_PI * b.semi_axes[0] * b.semi_axes[1] * b.semi_axes[2]);
+        b.density = ctx->density_h[i];
         b.cell = cell[i];
         b.fixed = fixed[i];
+        b.shape = ctx->shape_h[i];
     }
     return LBM_OK;
 }
@@ -1005,6 +1061,8 @@ lbm_status lbm_get_info(lbm_ctx *ctx, lbm_info *info) {
     info->sweep_block = ctx->variant == SWEEP_RING ? 0 : (ctx->variant == SWEEP_STAGED ? -1 : ctx->block);
     info->bytes_per_population = ctx->esize;
     info->sweep_split = (ctx->split && ctx->variant == SWEEP_DIRECT) ? 1 : 0;
+    info->remap_fused = fused_remap(ctx) ? 1 : 0;
+    info->remap_grid = fused_remap(ctx) ? ctx->remap_grid : 0;
     return LBM_OK;
 }
 
@@ -1101,6 +1159,14 @@ lbm_status lbm_set_sweep_split(lbm_ctx *ctx, int enable) {
     if (!ctx) return LBM_ERR_ARG;
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->split = enable != 0;
+    drop_graph(ctx);
+    return LBM_OK;
+}
+
+lbm_status lbm_set_remap_fused(lbm_ctx *ctx, int enable) {
+    if (!ctx) return LBM_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->remap_fused = enable != 0;
     drop_graph(ctx);
     return LBM_OK;
 }

@@ -130,9 +130,13 @@ struct PartDev {
 
 // FP32 copy of a body's pose and motion (PartDev::bodyf, BF_STRIDE floats per
 // body): rotation matrix, reciprocal semi-axes, centre as a double-float
-// (hi at BF_POS, lo at BF_POSLO), translational and angular velocity.
+// (hi at BF_POS, lo at BF_POSLO), translational and angular velocity, the
+// shape (BF_SHAPE: 0 ellipsoid, 1 spherocylinder) and, for a spherocylinder
+// of radius r and half length a, the half length of its cylindrical part in
+// units of r, (a - r) / r (BF_CAPH; 0 for an ellipsoid).
 constexpr int BF_STRIDE = 32;
-constexpr int BF_R = 0, BF_INV = 9, BF_POS = 12, BF_POSLO = 16, BF_U = 19, BF_W = 22;
+constexpr int BF_R = 0, BF_INV = 9, BF_POS = 12, BF_POSLO = 16, BF_U = 19, BF_W = 22, BF_CAPH = 25,
+              BF_SHAPE = 26;
 
 struct SweepArgs {
     LatDev lat0;             // copy of lattice 0 (used when nlat == 1)
@@ -340,6 +344,19 @@ cudaError_t launch_tile_bits(const RemapArgs &a, int ntiles, cudaStream_t s);
 cudaError_t launch_rigid_body(const RemapArgs &a, cudaStream_t s);
 cudaError_t launch_remap_step(int prec, int next_parity, const RemapArgs &a, int blocks_per_body,
                               cudaStream_t s);
+// Fused re-mapping step (rigid-body update and the four region passes in one
+// cooperative launch with grid barriers).  GridBar: zero-initialised device
+// state of the barrier, left at count 0 by every completed launch.
+struct GridBar {
+    unsigned count, gen;
+};
+// Co-resident blocks of the fused kernel over the device (0: no cooperative launch).
+int remap_fused_max_blocks();
+// Launch form the device and driver accept eagerly and in a captured graph:
+// 2 cooperative with a programmatic dependency, 1 cooperative, 0 none.
+int remap_fused_probe();
+cudaError_t launch_remap_fused(int prec, int next_parity, const RemapArgs &a, int blocks_per_body, int grid,
+                               int mode, GridBar *bar, cudaStream_t s);
 cudaError_t launch_clear_particles(const LatDev &h, const RemapArgs &a, int lat_index,
                                    cudaStream_t s);
 cudaError_t launch_claim_all(const RemapArgs &a, int blocks_per_body, cudaStream_t s);

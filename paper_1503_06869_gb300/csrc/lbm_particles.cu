@@ -45,16 +45,27 @@ __device__ __forceinline__ double min_image_rn(double d, int n, int periodic) {
     return d;
 }
 
-// Cell centre (i,j,k) inside the ellipsoid: (p0/a)^2 + (p1/b)^2 + (p2/c)^2 <= 1
-// with p = R^T d and d the nearest-image displacement from the centre.
+// Cell centre (i,j,k) inside the body (Sec. 4.2), with p = R^T d and d the
+// nearest-image displacement from the centre: ellipsoid
+// (p0/a)^2 + (p1/b)^2 + (p2/c)^2 <= 1; spherocylinder of radius r = b and half
+// length a along body x: t^2 + p1^2 + p2^2 <= r^2 with t = max(|p0| - (a - r), 0)
+// (distance to the axis segment at most r).  Every operation rounds once, in
+// the order written.
 __device__ __forceinline__ bool inside_rn(const LatDev &L, const double *pos, const double R[9],
-                                          const double *semi, int i, int j, int k) {
+                                          const double *semi, int shape, int i, int j, int k) {
     const double d0 = min_image_rn(__dsub_rn((double)i, pos[0]), L.nx, L.px);
     const double d1 = min_image_rn(__dsub_rn((double)j, pos[1]), L.ny, L.py);
     const double d2 = min_image_rn(__dsub_rn((double)k, pos[2]), L.nz, L.pz);
     const double p0 = __dadd_rn(__dadd_rn(__dmul_rn(R[0], d0), __dmul_rn(R[3], d1)), __dmul_rn(R[6], d2));
     const double p1 = __dadd_rn(__dadd_rn(__dmul_rn(R[1], d0), __dmul_rn(R[4], d1)), __dmul_rn(R[7], d2));
     const double p2 = __dadd_rn(__dadd_rn(__dmul_rn(R[2], d0), __dmul_rn(R[5], d1)), __dmul_rn(R[8], d2));
+    if (shape == 1) {
+        const double r = semi[1];
+        double t = __dsub_rn(fabs(p0), __dsub_rn(semi[0], r));
+        if (t < 0.0) t = 0.0;
+        const double s = __dadd_rn(__dadd_rn(__dmul_rn(t, t), __dmul_rn(p1, p1)), __dmul_rn(p2, p2));
+        return s <= __dmul_rn(r, r);
+    }
     const double t0 = __ddiv_rn(p0, semi[0]), t1 = __ddiv_rn(p1, semi[1]), t2 = __ddiv_rn(p2, semi[2]);
     const double s = __dadd_rn(__dadd_rn(__dmul_rn(t0, t0), __dmul_rn(t1, t1)), __dmul_rn(t2, t2));
     return s <= 1.0;
@@ -66,11 +77,15 @@ __device__ __forceinline__ bool inside_rn(const LatDev &L, const double *pos, co
 // the FP32 decision equals the FP64 one, and inside the band the exact FP64
 // test decides.  The result is bit-identical to inside_rn.
 // FP32 copy of a body's pose for that pre-test (from PartDev::bodyf:
-// rotation, reciprocal semi-axes, centre).
+// rotation, reciprocal semi-axes, centre, shape).  Both shapes share one
+// form, s = max(|p0/a'| - h, 0)^2 + (p1/b)^2 + (p2/c)^2: h = 0 and a' = a for
+// an ellipsoid, h = (a - r)/r and a' = b = c = r for a spherocylinder.
 struct BodyF32 {
     float R[9];
     float inv[3];
     float pos[3], poslo[3];  // centre as a double-float
+    float caph;
+    int shape;
 };
 
 __device__ __forceinline__ void load_body_f32(const float *src, BodyF32 &b) {
@@ -78,6 +93,8 @@ __device__ __forceinline__ void load_body_f32(const float *src, BodyF32 &b) {
     for (int k = 0; k < 3; ++k) b.inv[k] = src[BF_INV + k];
     for (int k = 0; k < 3; ++k) b.pos[k] = src[BF_POS + k];
     for (int k = 0; k < 3; ++k) b.poslo[k] = src[BF_POSLO + k];
+    b.caph = src[BF_CAPH];
+    b.shape = (int)src[BF_SHAPE];
 }
 
 // Displacement x - x_C of a cell coordinate from a body centre held as the
@@ -109,7 +126,7 @@ __device__ __forceinline__ bool inside_fast(const LatDev &L, const double *pos, 
     const float d0 = disp_f(i, b.pos[0], b.poslo[0], L.nx, L.px, sw);
     const float d1 = disp_f(j, b.pos[1], b.poslo[1], L.ny, L.py, sw);
     const float d2 = disp_f(k, b.pos[2], b.poslo[2], L.nz, L.pz, sw);
-    const float t0 = (b.R[0] * d0 + b.R[3] * d1 + b.R[6] * d2) * b.inv[0];
+    const float t0 = fmaxf(fabsf((b.R[0] * d0 + b.R[3] * d1 + b.R[6] * d2) * b.inv[0]) - b.caph, 0.0f);
     const float t1 = (b.R[1] * d0 + b.R[4] * d1 + b.R[7] * d2) * b.inv[1];
     const float t2 = (b.R[2] * d0 + b.R[5] * d1 + b.R[8] * d2) * b.inv[2];
     const float s = t0 * t0 + t1 * t1 + t2 * t2;
@@ -117,7 +134,7 @@ __device__ __forceinline__ bool inside_fast(const LatDev &L, const double *pos, 
         if (s < 0.999f) return true;
         if (s > 1.001f) return false;
     }
-    return inside_rn(L, pos, R64, semi, i, j, k);
+    return inside_rn(L, pos, R64, semi, b.shape, i, j, k);
 }
 
 // ---------------------------------------------------------------------------
@@ -166,12 +183,9 @@ __device__ __forceinline__ double quat_entry_rn(int e, double w, double x, doubl
 // every vector, lane e < 9 entry e of the rotation -- so that the FP64 work,
 // which GB300 issues at a low rate per warp instruction, takes few
 // instructions.  Every load is issued up front, every store at the end.
-__global__ void rigid_body_kernel(RemapArgs a) {
-    pdl_enter();
+__device__ void rigid_unit(const RemapArgs &a, int warp, int lane) {
     static_assert(ACC_COPIES == 32, "one lane per accumulator copy");
     const unsigned full = 0xffffffffu;
-    const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
     const PartDev &P = a.P;
     // warps [0, np) update the bodies, warps [np, np + nlat) hand over the walls
     if (warp >= P.np) {
@@ -220,11 +234,16 @@ __global__ void rigid_body_kernel(RemapArgs a) {
     if (lane < 4) P.quat_old[4 * t + lane] = lane == 0 ? w : sel3(lane - 1, x, y, z);
     const double F = hF + eF, M = hM + eM;
     bool finite = isfinite(F) && isfinite(M);
-    // old box half extent along k (FP32; the box only has to contain the body)
-    const float sf0 = (float)s0, sf1 = (float)s1, sf2 = (float)s2;
+    // old box half extent along k (FP32; the box only has to contain the
+    // body): ellipsoid sqrt(sum_j (R_kj s_j)^2); spherocylinder (radius
+    // s1, half length s0) |R_k0| (s0 - s1) + s1, the same form with the
+    // ellipsoid's first semi-axis replaced by s1 and the segment term added
+    const bool capsule = P.bodyf[BF_STRIDE * t + BF_SHAPE] != 0.0f;
+    const float sf0 = capsule ? (float)s1 : (float)s0, sf1 = (float)s1, sf2 = (float)s2;
+    const float seg = capsule ? (float)(s0 - s1) : 0.0f;
     auto half = [&](float r0, float r1, float r2) {
         const float e0 = r0 * sf0, e1 = r1 * sf1, e2 = r2 * sf2;
-        return sqrtf(e0 * e0 + e1 * e1 + e2 * e2) * 1.0001f;
+        return (sqrtf(e0 * e0 + e1 * e1 + e2 * e2) + fabsf(r0) * seg) * 1.0001f;
     };
     const float hold = half((float)Rr0, (float)Rr1, (float)Rr2);
     double posn = pos, veln = vel, omn = om, Ln = Lm, wn = w, xn = x, yn = y, zn = z;
@@ -327,6 +346,11 @@ __global__ void rigid_body_kernel(RemapArgs a) {
     P.region[6 * t + 3 + k] = max(ihi - ilo + 1, 0);
 }
 
+__global__ void rigid_body_kernel(RemapArgs a) {
+    pdl_enter();
+    rigid_unit(a, (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), threadIdx.x & 31);
+}
+
 // ---------------------------------------------------------------------------
 // re-mapping passes
 // ---------------------------------------------------------------------------
@@ -352,23 +376,24 @@ __device__ __forceinline__ bool region_cell(const int *reg, const LatDev &L, int
     return true;
 }
 
-// Region kernels run a 1-D grid of np * bpb blocks: body p = blockIdx.x / bpb.
+// The region passes work on np * bpb units of one block each: unit u covers
+// body p = u / bpb.  The separate kernels run one unit per block; the fused
+// kernel loops its blocks over the units.
 struct RegionLoop {
     int p, first, stride;
 };
 
-__device__ __forceinline__ RegionLoop region_loop(int bpb) {
+__device__ __forceinline__ RegionLoop region_loop(int unit, int bpb) {
     RegionLoop l;
-    l.p = blockIdx.x / bpb;
-    l.first = (blockIdx.x % bpb) * blockDim.x + threadIdx.x;
+    l.p = unit / bpb;
+    l.first = (unit % bpb) * blockDim.x + threadIdx.x;
     l.stride = bpb * blockDim.x;
     return l;
 }
 
 template <int PASS>
-__global__ void remap_region_kernel(RemapArgs a, int bpb) {
-    pdl_enter();
-    const RegionLoop rl = region_loop(bpb);
+__device__ void remap_region(const RemapArgs &a, int unit, int bpb) {
+    const RegionLoop rl = region_loop(unit, bpb);
     const int p = rl.p;
     const PartDev &P = a.P;
     if (p >= P.np) return;
@@ -396,6 +421,12 @@ __global__ void remap_region_kernel(RemapArgs a, int bpb) {
             }
         }
     }
+}
+
+template <int PASS>
+__global__ void remap_region_kernel(RemapArgs a, int bpb) {
+    pdl_enter();
+    remap_region<PASS>(a, blockIdx.x, bpb);
 }
 
 // Equilibrium offset f^eq_q(rho0, u) - w_q rho0 (Eq. fequ_Incompr).
@@ -492,9 +523,8 @@ __device__ void fixup_cell(const RemapArgs &a, const LatDev &L, int i, int j, in
 }
 
 template <int PREC, int NEXT_ODD>
-__global__ void fixup_region_kernel(RemapArgs a, int bpb) {
-    pdl_enter();
-    const RegionLoop rl = region_loop(bpb);
+__device__ void fixup_region(const RemapArgs &a, int unit, int bpb) {
+    const RegionLoop rl = region_loop(unit, bpb);
     const int p = rl.p;
     const PartDev &P = a.P;
     if (p >= P.np) return;
@@ -515,6 +545,12 @@ __global__ void fixup_region_kernel(RemapArgs a, int bpb) {
         if (owner != (uint32_t)p) continue;
         fixup_cell<PREC, NEXT_ODD>(a, L, c.i, c.j, c.k, false);
     }
+}
+
+template <int PREC, int NEXT_ODD>
+__global__ void fixup_region_kernel(RemapArgs a, int bpb) {
+    pdl_enter();
+    fixup_region<PREC, NEXT_ODD>(a, blockIdx.x, bpb);
 }
 
 // Flag byte of cell (i,j,k) from the particle-id map, and for a fluid cell
@@ -556,9 +592,8 @@ __device__ __forceinline__ uint8_t flag_of(const LatDev &L, const uint32_t *pid,
     return F_NEAR;
 }
 
-__global__ void flags_region_kernel(RemapArgs a, int bpb) {
-    pdl_enter();
-    const RegionLoop rl = region_loop(bpb);
+__device__ void flags_region(const RemapArgs &a, int unit, int bpb) {
+    const RegionLoop rl = region_loop(unit, bpb);
     const int p = rl.p;
     const PartDev &P = a.P;
     if (p >= P.np) return;
@@ -585,6 +620,75 @@ __global__ void flags_region_kernel(RemapArgs a, int bpb) {
         }
     }
 }
+
+__global__ void flags_region_kernel(RemapArgs a, int bpb) {
+    pdl_enter();
+    flags_region(a, blockIdx.x, bpb);
+}
+
+// Grid-wide barrier of the fused re-mapping kernel, whose blocks are all
+// resident (cooperative launch).  count: blocks arrived at the current
+// barrier; gen: barriers completed.  Thread 0 of each block reads gen before
+// it arrives (gen cannot move before every block has arrived); the last block
+// to arrive resets count and advances gen, the others poll gen, at most
+// 2^20 times.  Returns false after setting ERR_TIMEOUT when the poll ran out.
+__device__ bool grid_barrier(GridBar *b, uint32_t *err) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int good = 1;
+        const unsigned g = *(volatile unsigned *)&b->gen;
+        __threadfence();
+        if (atomicAdd(&b->count, 1u) == gridDim.x - 1) {
+            atomicExch(&b->count, 0u);
+            __threadfence();
+            atomicAdd(&b->gen, 1u);
+        } else {
+            unsigned it = 0;
+            while (*(volatile unsigned *)&b->gen == g) {
+                if (++it == (1u << 20)) {
+                    good = 0;
+                    atomicOr(err, ERR_TIMEOUT);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+constexpr int REMAP_BLOCK = 256;
+
+// The whole re-mapping step in one cooperative launch: rigid-body update of
+// every body (and wall hand-over), then uncover, claim, population fix-up and
+// flags, each pass over all np * bpb region units, with a grid barrier between
+// passes in place of the kernel boundaries of the separate launches.  The
+// arithmetic of every pass is that of the separate kernels.
+template <int PREC, int NEXT_ODD>
+__global__ void __launch_bounds__(REMAP_BLOCK) remap_fused_kernel(RemapArgs a, int bpb, GridBar *bar) {
+    pdl_enter();
+    const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    for (int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); w < a.P.np + a.nlat; w += nwarps)
+        rigid_unit(a, w, lane);
+    const int units = bpb * a.P.np;
+    if (!grid_barrier(bar, a.err)) return;
+    for (int u = blockIdx.x; u < units; u += gridDim.x) remap_region<0>(a, u, bpb);
+    if (!grid_barrier(bar, a.err)) return;
+    for (int u = blockIdx.x; u < units; u += gridDim.x) remap_region<1>(a, u, bpb);
+    if (!grid_barrier(bar, a.err)) return;
+    for (int u = blockIdx.x; u < units; u += gridDim.x) fixup_region<PREC, NEXT_ODD>(a, u, bpb);
+    if (!grid_barrier(bar, a.err)) return;
+    for (int u = blockIdx.x; u < units; u += gridDim.x) flags_region(a, u, bpb);
+}
+
+// Empty cooperative kernel: tells whether cooperative launches (with a
+// programmatic dependency) are accepted, eagerly and in a captured graph.
+__global__ void coop_probe_kernel() { pdl_enter(); }
 
 // One block per 32 tiles (one word of tile bits); warp w scans tiles w, w+8,
 // w+16, w+24 of the word.
@@ -830,8 +934,6 @@ __global__ void link_write_kernel(const LatDev *lat, const uint8_t *flags, const
     }
 }
 
-constexpr int REMAP_BLOCK = 256;
-
 template <int PREC>
 cudaError_t remap_step_prec(int next_parity, const RemapArgs &a, int bpb, cudaStream_t s) {
     const unsigned grid = (unsigned)bpb * (unsigned)a.P.np;
@@ -842,6 +944,24 @@ cudaError_t remap_step_prec(int next_parity, const RemapArgs &a, int bpb, cudaSt
                         : launch_pdl(fixup_region_kernel<PREC, 0>, grid, REMAP_BLOCK, 0, s, a, bpb);
     if (e == cudaSuccess) e = launch_pdl(flags_region_kernel, grid, REMAP_BLOCK, 0, s, a, bpb);
     return e;
+}
+
+template <int PREC>
+cudaError_t remap_fused_prec(int next_parity, const RemapArgs &a, int bpb, int grid, int mode, GridBar *bar,
+                             cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(REMAP_BLOCK);
+    cfg.stream = s;
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = mode == 2 ? 2 : 1;
+    return next_parity ? cudaLaunchKernelEx(&cfg, remap_fused_kernel<PREC, 1>, a, bpb, bar)
+                       : cudaLaunchKernelEx(&cfg, remap_fused_kernel<PREC, 0>, a, bpb, bar);
 }
 
 template <int PREC>
@@ -883,6 +1003,84 @@ cudaError_t set_pdfs_prec(int next_parity, const LatDev &h, const LatDev *d, voi
 
 int kernels_per_remap_step() { return 4; }
 
+int remap_fused_max_blocks() {
+    int dev = 0, sms = 0, coop = 0, nb = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (!coop || sms <= 0) return 0;
+    // every instantiation has the same launch bounds; the largest footprint decides
+    int lo = 1 << 30;
+    const void *ks[] = {(const void *)remap_fused_kernel<LBM_F64, 0>, (const void *)remap_fused_kernel<LBM_F64, 1>,
+                        (const void *)remap_fused_kernel<LBM_F32, 0>, (const void *)remap_fused_kernel<LBM_F32, 1>,
+                        (const void *)remap_fused_kernel<LBM_F16_OFFSET, 0>,
+                        (const void *)remap_fused_kernel<LBM_F16_OFFSET, 1>,
+                        (const void *)remap_fused_kernel<LBM_BF16_OFFSET, 0>,
+                        (const void *)remap_fused_kernel<LBM_BF16_OFFSET, 1>};
+    for (const void *k : ks) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, REMAP_BLOCK, 0) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        lo = nb < lo ? nb : lo;
+    }
+    return lo > 0 ? lo * sms : 0;
+}
+
+int remap_fused_probe() {
+    if (remap_fused_max_blocks() <= 0) return 0;
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    auto launch = [&](int mode) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(2);
+        cfg.blockDim = dim3(32);
+        cfg.stream = st;
+        cudaLaunchAttribute at[2];
+        at[0].id = cudaLaunchAttributeCooperative;
+        at[0].val.cooperative = 1;
+        at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[1].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = mode == 2 ? 2 : 1;
+        return cudaLaunchKernelEx(&cfg, coop_probe_kernel);
+    };
+    // a cooperative launch between two ordinary programmatic launches, as in a step
+    auto sequence = [&](int mode) {
+        cudaError_t e = launch_pdl(coop_probe_kernel, 1, 32, 0, st);
+        if (e == cudaSuccess) e = launch(mode);
+        if (e == cudaSuccess) e = launch_pdl(coop_probe_kernel, 1, 32, 0, st);
+        return e;
+    };
+    int best = 0;
+    for (int mode = 2; mode >= 1 && !best; --mode) {
+        cudaError_t e = sequence(mode);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) {
+            cudaGraph_t g = nullptr;
+            cudaGraphExec_t x = nullptr;
+            e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                const cudaError_t el = sequence(mode);
+                e = cudaStreamEndCapture(st, &g);
+                if (e == cudaSuccess) e = el;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&x, g, 0);
+            if (e == cudaSuccess) e = cudaGraphLaunch(x, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (x) cudaGraphExecDestroy(x);
+            if (g) cudaGraphDestroy(g);
+        }
+        if (e == cudaSuccess) best = mode;
+        cudaGetLastError();
+    }
+    cudaStreamDestroy(st);
+    return best;
+}
+
 cudaError_t launch_tile_bits(const RemapArgs &a, int ntiles, cudaStream_t s) {
     if (!a.tbits || ntiles <= 0) return cudaSuccess;
     return launch_pdl(tile_bits_kernel, (ntiles + 31) / 32, 256, 0, s, a, ntiles);
@@ -910,6 +1108,18 @@ cudaError_t launch_remap_step(int prec, int next_parity, const RemapArgs &a, int
     case LBM_F32: return remap_step_prec<LBM_F32>(next_parity, a, bpb, s);
     case LBM_F16_OFFSET: return remap_step_prec<LBM_F16_OFFSET>(next_parity, a, bpb, s);
     case LBM_BF16_OFFSET: return remap_step_prec<LBM_BF16_OFFSET>(next_parity, a, bpb, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_remap_fused(int prec, int next_parity, const RemapArgs &a, int bpb, int grid, int mode,
+                               GridBar *bar, cudaStream_t s) {
+    if (a.P.np <= 0 || grid <= 0 || mode <= 0) return cudaErrorInvalidValue;
+    switch (prec) {
+    case LBM_F64: return remap_fused_prec<LBM_F64>(next_parity, a, bpb, grid, mode, bar, s);
+    case LBM_F32: return remap_fused_prec<LBM_F32>(next_parity, a, bpb, grid, mode, bar, s);
+    case LBM_F16_OFFSET: return remap_fused_prec<LBM_F16_OFFSET>(next_parity, a, bpb, grid, mode, bar, s);
+    case LBM_BF16_OFFSET: return remap_fused_prec<LBM_BF16_OFFSET>(next_parity, a, bpb, grid, mode, bar, s);
     }
     return cudaErrorInvalidValue;
 }

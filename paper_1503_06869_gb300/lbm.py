@@ -45,14 +45,15 @@ class lbm_grid_desc(C.Structure):
 class lbm_particle(C.Structure):
     _fields_ = [("pos", D3), ("quat", C.c_double * 4), ("vel", D3), ("omega", D3),
                 ("semi_axes", D3), ("density", C.c_double), ("ext_force", D3),
-                ("ext_torque", D3), ("cell", C.c_int), ("fixed", C.c_int)]
+                ("ext_torque", D3), ("cell", C.c_int), ("fixed", C.c_int), ("shape", C.c_int)]
 
 
 class lbm_info(C.Structure):
     _fields_ = [("ncells_total", C.c_longlong), ("nfluid_hint", C.c_longlong),
                 ("nlattices", C.c_int), ("nparticles", C.c_int), ("steps_done", C.c_longlong),
                 ("device_bytes", C.c_size_t), ("sweep_grid", C.c_int), ("sweep_block", C.c_int),
-                ("bytes_per_population", C.c_int), ("sweep_split", C.c_int)]
+                ("bytes_per_population", C.c_int), ("sweep_split", C.c_int),
+                ("remap_fused", C.c_int), ("remap_grid", C.c_int)]
 
 
 # name -> (restype, argtypes) for every entry point of include/lbm.h
@@ -78,6 +79,7 @@ SIGNATURES = {
     "lbm_autotune": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "lbm_set_graphs": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_set_sweep_split": (C.c_int, [C.c_void_p, C.c_int]),
+    "lbm_set_remap_fused": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_set_sweep_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_get_sweep_timing": (C.c_int, [C.c_void_p, C.POINTER(C.c_double),
                                        C.POINTER(C.c_longlong)]),
@@ -235,6 +237,10 @@ def lbm_set_sweep_split(ctx, enable: bool):
     _check(load().lbm_set_sweep_split(ctx, 1 if enable else 0), ctx)
 
 
+def lbm_set_remap_fused(ctx, enable: bool):
+    _check(load().lbm_set_remap_fused(ctx, 1 if enable else 0), ctx)
+
+
 def lbm_set_graphs(ctx, enable: bool):
     _check(load().lbm_set_graphs(ctx, int(bool(enable))), ctx)
 
@@ -377,13 +383,14 @@ def particle_struct(p) -> lbm_particle:
     s.density = p.density
     s.cell = p.cell
     s.fixed = p.fixed
+    s.shape = getattr(p, "shape", 0)
     return s
 
 
 def particle_array(parts: Sequence[lbm_particle]) -> np.ndarray:
     """Particle structs -> records (pos3 quat4 vel3 omega3 semi3 density extF3
-    extM3 fixed cell), the layout the tests compare."""
-    out = np.zeros((len(parts), 25))
+    extM3 fixed cell shape), the layout the tests compare."""
+    out = np.zeros((len(parts), 26))
     for i, s in enumerate(parts):
         out[i, 0:3] = list(s.pos)
         out[i, 3:7] = list(s.quat)
@@ -395,6 +402,7 @@ def particle_array(parts: Sequence[lbm_particle]) -> np.ndarray:
         out[i, 20:23] = list(s.ext_torque)
         out[i, 23] = s.fixed
         out[i, 24] = s.cell
+        out[i, 25] = s.shape
     return out
 
 

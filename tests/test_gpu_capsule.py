@@ -1,0 +1,161 @@
+"""Spherocylinders (the particles of Sec. 5.1, Fig. Capsule) on the GPU.
+
+Parity: the CUDA path against the FP64 oracle for spinning and translating
+spherocylinders (bit-exact flags and particle ids, the usual velocity
+tolerances), alone in a closed no-slip box, together with an ellipsoid, and
+across a periodic boundary.
+
+Rotational validation (Sec. 5.1-5.2, Appendix A table): a spherocylinder of
+radius r = 4 dx and aspect ratio L / r under the constant torque M_x of the
+torque table, water (nu = 1e-6 m^2/s, rho_f = 1e3 kg/m^3), dx = 1e-5 m,
+tau = 6, rho_p = 1195 kg/m^3, in a closed no-slip cube.  The mean angular
+velocity over the last half of the run (sampled every 200 steps) is compared
+with the paper's LBM result omega*_LBM; the band is the paper's own spread
+delta_omega = (max - min) / mean of its samples (at least 3 %).  The paper used
+an 816^3 cube and reports the wall influence on rotation as negligible; the
+cubes here are 6-8 body lengths wide.  It also checks that omega lies between
+Tirado's cylinders with and without the end caps, as the paper finds.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import closed_forms as cf
+from lbm_inputs import Lattice, Particle, SplitMix64, quat_from_axis, shear_lattice, SHAPE_SPHEROCYLINDER
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+TOL_U = {"f64": 1e-12, "f32": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1503_06869_gb300 import _build, lbm as L
+    _build.build()
+    L.load()
+    return L
+
+
+def capsule(pos, quat, half_length, r, **kw):
+    return Particle(pos=pos, quat=quat, semi_axes=(half_length, r, r), shape=SHAPE_SPHEROCYLINDER, **kw)
+
+
+def rel_l2(a, b, mask):
+    a, b = a[..., mask], b[..., mask]
+    den = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (den if den > 0 else 1.0)
+
+
+def compare(g, o, prec):
+    _, ug, fg, pg, _ = g.fields()
+    _, uo, fo, po, _ = o.fields()
+    assert np.array_equal(fg, fo), f"flags differ at {np.nonzero(fg != fo)[0][:10]}"
+    assert np.array_equal(pg, po), "particle-id maps differ"
+    e = rel_l2(ug, uo, fo == 0)
+    assert e <= TOL_U[prec], f"velocity rel L2 {e:.3e}"
+    Fg, Mg = g.forces()
+    Fo, Mo = o.forces()
+    s = max(np.abs(Mo).max(), np.abs(Fo).max(), 1e-300)
+    tol = 1e-9 if prec == "f64" else 1e-3
+    assert np.abs(Fg - Fo).max() <= tol * s and np.abs(Mg - Mo).max() <= tol * s
+    pgr, por = g.particles(), o.particles()
+    assert np.array_equal(pgr[:, 25], por[:, 25])
+    assert np.allclose(pgr[:, 0:16], por[:, 0:16], rtol=1e-10 if prec == "f64" else 1e-5, atol=1e-12)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_spinning_spherocylinder_in_closed_box(lbm, prec):
+    lat = Lattice(30, 26, 24, tau=0.9, periodic=(0, 0, 0))
+    rng = SplitMix64(21)
+    p = capsule((14.6, 12.7, 11.9), quat_from_axis(rng.unit_vector()), 7.0, 2.6, omega=(0.004, -0.002, 0.006),
+                ext_torque=(0.8, 0.0, -0.5), density=1.195)
+    g = lbm.Simulation(lat, [p], prec=prec)
+    o = oracle.Sim(lat, [p])
+    for c in (1, 2, 5, 12, 20):
+        g.step(c)
+        o.step(c)
+        compare(g, o, prec)
+    assert g.particles()[0, 25] == SHAPE_SPHEROCYLINDER
+
+
+def test_spherocylinder_and_ellipsoid_in_shear(lbm):
+    lat = shear_lattice(34, 22, 20, 0.8, 0.02)
+    rng = SplitMix64(22)
+    ps = [capsule((9.3, 10.6, 9.8), quat_from_axis(rng.unit_vector()), 6.0, 2.2, vel=(0.02, 0.0, 0.01),
+                  omega=(0.0, 0.01, 0.0), density=20.0),
+          Particle(pos=(24.2, 11.1, 10.4), quat=quat_from_axis(rng.unit_vector()), semi_axes=(5.0, 2.5, 2.0),
+                   vel=(-0.02, 0.0, 0.0), density=20.0)]
+    g = lbm.Simulation(lat, ps, prec="f64")
+    o = oracle.Sim(lat, ps)
+    for c in (3, 7, 20):
+        g.step(c)
+        o.step(c)
+        compare(g, o, "f64")
+
+
+def test_spherocylinder_across_periodic_boundary(lbm):
+    lat = Lattice(28, 20, 22, tau=0.7, periodic=(1, 1, 1))
+    rng = SplitMix64(23)
+    p = capsule((1.4, 9.6, 20.9), quat_from_axis(rng.unit_vector()), 5.5, 2.0, vel=(-0.06, 0.02, 0.05),
+                omega=(0.01, 0.0, -0.01), density=40.0)
+    g = lbm.Simulation(lat, [p], prec="f64")
+    o = oracle.Sim(lat, [p])
+    for c in (1, 4, 15):
+        g.step(c)
+        o.step(c)
+        compare(g, o, "f64")
+
+
+def test_rejects_inconsistent_spherocylinder(lbm):
+    lat = Lattice(20, 20, 20, periodic=(1, 1, 1))
+    with pytest.raises(lbm.LBMError):
+        lbm.Simulation(lat, [Particle(pos=(10, 10, 10), quat=(1, 0, 0, 0), semi_axes=(5.0, 2.0, 2.5),
+                                      shape=SHAPE_SPHEROCYLINDER)])
+    with pytest.raises(lbm.LBMError):
+        lbm.Simulation(lat, [Particle(pos=(10, 10, 10), quat=(1, 0, 0, 0), semi_axes=(1.5, 2.0, 2.0),
+                                      shape=SHAPE_SPHEROCYLINDER)])
+    with pytest.raises(lbm.LBMError):
+        lbm.Simulation(lat, [Particle(pos=(10, 10, 10), quat=(1, 0, 0, 0), semi_axes=(3.0, 2.0, 2.0), shape=7)])
+
+
+# --------------------------------------------------------------------------
+# rotational validation against the paper's LBM angular velocities
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("aspect,box,steps", [(4, 112, 24000), (8, 160, 40000), (14, 224, 60000)])
+def test_rotational_validation_against_table_A(lbm, aspect, box, steps):
+    gold = json.load(open(os.path.join(HERE, "golden", "table_A_tirado.json")))
+    col = gold["inverse_eps"].index(aspect)
+    dx, nu, rho_f, tau = 1e-5, 1e-6, 1e3, 6.0
+    dt = cf.lattice_time_step(tau, dx, nu)
+    r = 4.0
+    L = aspect * r
+    M_lat = gold["torque_x_1e-15"][col] * 1e-15 * dt * dt / (rho_f * dx ** 5)
+    c = (box - 1) / 2.0
+    q = (math.cos(math.pi / 4), 0.0, 0.0, math.sin(math.pi / 4))  # body axis along world y
+    p = capsule((c + 0.13, c - 0.21, c + 0.07), q, L / 2, r, density=1.195, ext_torque=(M_lat, 0.0, 0.0))
+    lat = Lattice(box, box, box, tau=tau, periodic=(0, 0, 0))
+    sim = lbm.Simulation(lat, [p], prec="f32")
+    every = 200
+    w = []
+    for _ in range(steps // every):
+        sim.step(every)
+        w.append(sim.particles()[0, 10])
+    sim.close()
+    w = np.array(w[len(w) // 2:]) / dt  # last half, in 1/s
+    mean = float(w.mean())
+    spread = float((w.max() - w.min()) / mean * 100)
+    ref, delta = gold["omega_LBM_1_s"][col], gold["delta_omega_pct"][col]
+    lo, hi = gold["omega_Tir_wC_1_s"][col], gold["omega_Tir_nC_1_s"][col]
+    print(f"aspect {aspect}: omega {mean:.4g} 1/s (paper {ref}, {100 * (mean / ref - 1):+.2f} %), spread "
+          f"{spread:.2f} % (paper {delta} %), Tirado wC {lo} / nC {hi}, box {box}^3, {steps} steps")
+    assert lo < mean < hi
+    assert abs(mean / ref - 1) <= max(delta, 3.0) / 100
