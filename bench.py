@@ -274,8 +274,8 @@ def main():
     ap.add_argument("--prec", default="f32", choices=["f64", "f32", "f16", "bf16"])
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--remap-separate", action="store_true",
-                    help="run the re-mapping step as five launches instead of one cooperative launch")
+    ap.add_argument("--remap-fused", action="store_true",
+                    help="run the re-mapping step as one cooperative launch instead of five launches")
     args = ap.parse_args()
     rank, world, local = dist_setup(args.gpus)
     w = workload(args.workload)
@@ -293,8 +293,8 @@ def main():
         # throughput only: the parameters are seeded and small, not trained
         theta = np.random.default_rng(0).normal(size=lbm.CLOSURE_PARAMS) * 0.01
         lbm.lbm_set_closure(h, theta.astype(np.float16))
-    if args.remap_separate:
-        lbm.lbm_set_remap_fused(h, False)
+    if args.remap_fused:
+        lbm.lbm_set_remap_fused(h, True)
     lbm.lbm_autotune(h)
     info = lbm.lbm_get_info(h)
     sim.step(args.warmup)

@@ -260,16 +260,18 @@ lbm_status lbm_set_launch(lbm_ctx *ctx, int block, int grid);
  * takes effect at the next lbm_step. */
 lbm_status lbm_set_sweep_split(lbm_ctx *ctx, int enable);
 
-/* Fused re-mapping step (enable != 0, the default): the rigid-body update
+/* Fused re-mapping step (enable != 0; default 0): the rigid-body update
  * (Sec. 4.3) and the four passes of the obstacle re-mapping (Sec. 4.2:
  * uncover, claim, refill/fix-up, flags) run as one cooperative launch of at
  * most one resident wave, with grid-wide barriers between the passes, instead
  * of five launches.  Used only where the device and driver accept cooperative
  * launches (probed once per context, eagerly and inside a captured graph);
- * otherwise, or with enable = 0, the separate kernels run.  Results are
- * identical either way.  A barrier wait that runs out (it cannot while the
- * launch is resident) makes lbm_step return LBM_ERR_TIMEOUT.  Takes effect at
- * the next lbm_step. */
+ * otherwise the separate kernels run.  The arithmetic is the same either way
+ * (results differ only by the order of the sweep's FP64 force atomics).  On
+ * GB300 the five launches with programmatic dependent launch are faster, so
+ * the default is the separate form.  A barrier wait that runs out (it cannot
+ * while the launch is resident) makes lbm_step return LBM_ERR_TIMEOUT.  Takes
+ * effect at the next lbm_step. */
 lbm_status lbm_set_remap_fused(lbm_ctx *ctx, int enable);
 
 /* Choose the sweep launch shape by timing candidates on this context (runs

@@ -64,8 +64,9 @@ struct lbm_ctx {
     // 0 unavailable, 1 cooperative, 2 cooperative + programmatic dependency),
     // user switch, grid and barrier state
     int remap_mode = -1;
-    bool remap_fused = true;
+    bool remap_fused = false;
     int remap_grid = 0;
+    int np_pending = 0;             // bodies the launch shape was computed for
     GridBar *gbar = nullptr;
 
     bool graphs = true;
@@ -201,6 +202,17 @@ SweepArgs sweep_args(lbm_ctx *ctx) {
 
 // kernels one sweep issues (the split direct sweep: list, sweep, near cells)
 int sweep_kernels(const lbm_ctx *ctx) { return (ctx->split && ctx->variant == SWEEP_DIRECT) ? 3 : 1; }
+
+// Fused re-mapping launch: probed on first use; one resident wave at most,
+// no more blocks than region units.
+void update_remap_grid(lbm_ctx *ctx) {
+    ctx->remap_grid = 0;
+    if (!ctx->remap_fused || ctx->np_pending <= 0) return;
+    if (ctx->remap_mode < 0) ctx->remap_mode = remap_fused_probe();
+    const long long units = (long long)ctx->remap_bpb * ctx->np_pending;
+    const long long wave = ctx->remap_mode > 0 ? remap_fused_max_blocks() : 0;
+    ctx->remap_grid = (int)(units < wave ? units : wave);
+}
 
 bool fused_remap(const lbm_ctx *ctx) {
     return ctx->remap_fused && ctx->remap_mode > 0 && ctx->np > 0 && ctx->remap_grid > 0;
@@ -702,11 +714,8 @@ lbm_status lbm_set_particles(lbm_ctx *ctx, const lbm_particle *p, int n) {
         const long long cap = (long long)(sms > 0 ? sms : 1) * 64;
         if (n > 0 && bpb * n > cap) bpb = cap / n > 0 ? cap / n : 1;
         ctx->remap_bpb = (int)bpb;
-        // fused step: one resident wave at most, no more blocks than units
-        if (n > 0 && ctx->remap_mode < 0) ctx->remap_mode = remap_fused_probe();
-        const long long units = bpb * n;
-        const long long wave = ctx->remap_mode > 0 ? remap_fused_max_blocks() : 0;
-        ctx->remap_grid = (int)(units < wave ? units : wave);
+        ctx->np_pending = n;
+        update_remap_grid(ctx);
     }
     CK(cudaStreamSynchronize(ctx->stream));
     drop_graph(ctx);
@@ -1167,6 +1176,7 @@ lbm_status lbm_set_remap_fused(lbm_ctx *ctx, int enable) {
     if (!ctx) return LBM_ERR_ARG;
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->remap_fused = enable != 0;
+    update_remap_grid(ctx);
     drop_graph(ctx);
     return LBM_OK;
 }

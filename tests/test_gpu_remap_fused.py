@@ -27,6 +27,9 @@ def lbm():
 
 
 RTOL = {"f64": 1e-11, "f32": 1e-5, "f16": 1e-2}
+# force and torque: sums of many link terms that largely cancel (the parity
+# tests' force tolerances)
+RTOL_FM = {"f64": 1e-9, "f32": 1e-4, "f16": 5e-2}
 
 
 def state(sim, ncell):
@@ -46,7 +49,7 @@ def same(a, b, prec):
         else:
             scale = max(np.abs(b[k]).max(), 1e-300)
             err = np.abs(a[k] - b[k]).max() / scale
-            assert err <= RTOL[prec], (k, err)
+            assert err <= (RTOL_FM if k == "FM" else RTOL)[prec], (k, err)
 
 
 def run(L, w, prec, fused, steps, graphs=True):
