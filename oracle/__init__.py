@@ -75,7 +75,8 @@ def _declare(lib):
     lib.orc_omega_odd.argtypes = [C.c_double, C.c_double]
     lib.orc_equilibrium.argtypes = [C.c_double, C.c_void_p, C.c_double, C.c_void_p]
     lib.orc_collide_cell.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_void_p,
-                                     C.c_void_p]
+                                     C.c_void_p, C.c_void_p]
+    lib.orc_set_momentum_stabilisation.argtypes = [C.c_void_p, C.c_int]
     lib.orc_inside.restype = C.c_int
     lib.orc_inside.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int,
                                C.c_int, C.c_int]
@@ -137,11 +138,12 @@ def equilibrium(rho: float, u, rho0: float = 1.0) -> np.ndarray:
     return out
 
 
-def collide_cell(f, omega: float, omega_o: float, rho0: float = 1.0, g=(0.0, 0.0, 0.0)):
+def collide_cell(f, omega: float, omega_o: float, rho0: float = 1.0, g=(0.0, 0.0, 0.0), ubar=(0.0, 0.0, 0.0)):
     f = np.ascontiguousarray(f, dtype=np.float64)
     g = np.ascontiguousarray(g, dtype=np.float64)
+    ub = np.ascontiguousarray(ubar, dtype=np.float64)
     out = np.zeros(Q)
-    lib().orc_collide_cell(_ptr(f), omega, omega_o, rho0, _ptr(g), _ptr(out))
+    lib().orc_collide_cell(_ptr(f), omega, omega_o, rho0, _ptr(g), _ptr(ub), _ptr(out))
     return out
 
 
@@ -196,6 +198,9 @@ class Sim:
         self.np = 0
         if len(particles):
             self.set_particles(particles)
+
+    def set_momentum_stabilisation(self, enable: bool = True):
+        self._L.orc_set_momentum_stabilisation(self.h, 1 if enable else 0)
 
     def __del__(self):
         h = getattr(self, "h", None)

@@ -78,6 +78,8 @@ struct orc_sim {
     orc_particle *p;
     double Fwall[2][3];
     long t;
+    int stab;         /* momentum stabilisation on (Sec. 4.1) */
+    double ubar[3];   /* mean fluid velocity of the current step */
 };
 
 static int g_threads = 1;
@@ -129,11 +131,14 @@ static void moments(const double *f, double rho0, double *rho, double u[3]) {
 /* TRT collision of one cell (Eqs. TRTOp, EqPDF_TRT, LBMCollide):
    f~_q = f_q + lambda_e (f^e_q - f^eq,e_q) + lambda_o (f^o_q - f^eq,o_q),
    lambda_e = -omega, lambda_o = -omega_odd; plus the body-force source
-   3 w_q rho0 c_q.g. */
+   3 w_q rho0 c_q.g.  The equilibrium is taken at the velocity u - ubar:
+   ubar is the domain-mean velocity under momentum stabilisation (Sec. 4.1),
+   zero otherwise. */
 void orc_collide_cell(const double *f, double omega, double omega_odd, double rho0,
-                      const double g[3], double *ft) {
+                      const double g[3], const double ubar[3], double *ft) {
     double rho, u[3];
     moments(f, rho0, &rho, u);
+    for (int a = 0; a < 3; ++a) u[a] -= ubar[a];
     double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     for (int q = 0; q < Q; ++q) {
         int qb = OPP[q];
@@ -422,8 +427,30 @@ static void obstacle_velocity(const orc_sim *s, uint32_t id, int i, int j, int k
     }
 }
 
+/* Momentum stabilisation (Sec. 4.1): the mean velocity sum(c f)/rho0 over
+   the fluid cells of the whole domain, taken before the collision of this
+   step and subtracted from every cell's velocity in its equilibrium. */
+static void mean_fluid_velocity(orc_sim *s) {
+    double j[3] = {0.0, 0.0, 0.0}, cnt = 0.0;
+    for (long x = 0; x < s->n; ++x) {
+        if (s->flag[x] != FL_FLUID) continue;
+        double f[Q], rho, u[3];
+        for (int q = 0; q < Q; ++q) f[q] = s->f[q * s->n + x];
+        moments(f, s->rho0, &rho, u);
+        for (int a = 0; a < 3; ++a) j[a] += u[a];
+        cnt += 1.0;
+    }
+    for (int a = 0; a < 3; ++a) s->ubar[a] = cnt > 0.0 ? j[a] / cnt : 0.0;
+}
+
+void orc_set_momentum_stabilisation(orc_sim *s, int enable) {
+    s->stab = enable != 0;
+    for (int a = 0; a < 3; ++a) s->ubar[a] = 0.0;
+}
+
 static void collide_and_stream(orc_sim *s) {
     const long n = s->n;
+    if (s->stab) mean_fluid_velocity(s);
     for (int p = 0; p < s->np; ++p)
         for (int a = 0; a < 3; ++a) s->p[p].F[a] = s->p[p].M[a] = 0.0;
     for (int w = 0; w < 2; ++w)
@@ -448,7 +475,7 @@ static void collide_and_stream(orc_sim *s) {
                 long x = cell_index(s, i, j, k);
                 if (s->flag[x] != FL_FLUID) continue;
                 for (int q = 0; q < Q; ++q) f[q] = s->f[q * n + x];
-                orc_collide_cell(f, s->omega, s->omega_odd, s->rho0, s->g, ft);
+                orc_collide_cell(f, s->omega, s->omega_odd, s->rho0, s->g, s->ubar, ft);
                 for (int q = 0; q < Q; ++q) {
                     int ii = wrap(i + CX[q], s->nx), jj = wrap(j + CY[q], s->ny),
                         kk = wrap(k + CZ[q], s->nz);

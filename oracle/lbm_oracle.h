@@ -54,13 +54,16 @@ void orc_get_wall_forces(const orc_sim *s, double *f6);
 void orc_get_particles(const orc_sim *s, double *state);
 int orc_get_links(const orc_sim *s, int32_t *cell, int8_t *q, uint32_t *pid, int cap);
 void orc_set_threads(int nthreads);
+/* Momentum stabilisation (Sec. 4.1): each step's equilibria use u - ubar,
+   ubar the mean velocity of all fluid cells before that step's collision. */
+void orc_set_momentum_stabilisation(orc_sim *s, int enable);
 
 /* building blocks, exposed for the pin tests */
 void orc_lattice(int *cx, int *cy, int *cz, double *w, int *opp);
 double orc_omega_odd(double tau, double magic);
 void orc_equilibrium(double rho, const double u[3], double rho0, double *feq);
 void orc_collide_cell(const double *f, double omega, double omega_odd, double rho0,
-                      const double g[3], double *ft);
+                      const double g[3], const double ubar[3], double *ft);
 int orc_inside(const double *particle, int nx, int ny, int nz, const int periodic[3],
                int i, int j, int k);
 void orc_quat_to_matrix(const double q[4], double R[9]);
