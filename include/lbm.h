@@ -274,6 +274,16 @@ lbm_status lbm_set_sweep_split(lbm_ctx *ctx, int enable);
  * effect at the next lbm_step. */
 lbm_status lbm_set_remap_fused(lbm_ctx *ctx, int enable);
 
+/* Momentum stabilisation (Sec. 4.1; enable != 0; default 0): before every
+ * sweep the mean velocity ubar = sum(j) / (rho0 N_fluid) over all fluid cells
+ * of the current state is computed (two extra launches per step, one read of
+ * the populations), and every cell's equilibrium is taken at u - ubar, so
+ * that a fully periodic domain with constant forces on its particles does not
+ * accelerate without bound (the total fluid momentum relaxes by
+ * 1 - omega_odd per step).  Single-lattice contexts only: a batch returns
+ * LBM_ERR_UNSUPPORTED.  Takes effect at the next lbm_step. */
+lbm_status lbm_set_momentum_stabilisation(lbm_ctx *ctx, int enable);
+
 /* Choose the sweep launch shape by timing candidates on this context (runs
  * sweeps on scratch copies: the state is restored afterwards).  The chosen
  * shape is kept and returned through block/grid (either may be NULL). */

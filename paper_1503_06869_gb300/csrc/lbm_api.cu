@@ -68,6 +68,10 @@ struct lbm_ctx {
     int remap_grid = 0;
     int np_pending = 0;             // bodies the launch shape was computed for
     GridBar *gbar = nullptr;
+    // momentum stabilisation: sums and mean velocity (8 doubles), FP32 mean
+    bool stab = false;
+    double *stab_acc = nullptr;
+    float *stab_accf = nullptr;
 
     bool graphs = true;
     cudaGraphExec_t gexec = nullptr;
@@ -281,6 +285,12 @@ void drop_graph(lbm_ctx *ctx) {
 lbm_status enqueue_step(lbm_ctx *ctx, bool timed) {
     const int parity = (int)(ctx->t & 1);
     SweepArgs sa = sweep_args(ctx);
+    if (ctx->stab) {
+        // mean fluid velocity of the state this sweep reads (Sec. 4.1)
+        CK(launch_momentum_mean(ctx->prec, parity, ctx->lat_h[0], ctx->lat_d, ctx->f, ctx->flags, ctx->stab_acc,
+                                ctx->stab_accf, ctx->stream));
+        ctx->launches += 2;
+    }
     if (timed) {
         if (ctx->ev_used + 2 > ctx->ev.size()) {
             for (int i = 0; i < 64; ++i) {
@@ -510,6 +520,8 @@ lbm_status create_common(const lbm_grid_desc *cells, int ncells, lbm_ctx **out) 
     ctx->wall_last = (double *)owned_alloc(ctx, sizeof(double) * 6 * ncells);
     ctx->err = (uint32_t *)owned_alloc(ctx, 16);
     ctx->gbar = (GridBar *)owned_alloc(ctx, 16);
+    ctx->stab_acc = (double *)owned_alloc(ctx, 64);
+    ctx->stab_accf = (float *)owned_alloc(ctx, 16);
     {
         long long tiles32 = 0;  // tiles of the smallest direct-sweep tile (32 cells)
         for (auto &L : ctx->lat_h) tiles32 += (L.n + 31) / 32;
@@ -517,7 +529,7 @@ lbm_status create_common(const lbm_grid_desc *cells, int ncells, lbm_ctx **out) 
     }
     if (!ctx->lat_d || !ctx->f || !ctx->flags || !ctx->pid || !ctx->pid_prev || !ctx->wall_acc ||
         !ctx->wall_last || !ctx->err || !ctx->tbits || !ctx->links || !ctx->nbody || !ctx->near_list ||
-        !ctx->near_count || !ctx->gbar) {
+        !ctx->near_count || !ctx->gbar || !ctx->stab_acc || !ctx->stab_accf) {
         lbm_destroy(ctx);
         return LBM_ERR_OOM;
     }
@@ -534,7 +546,9 @@ lbm_status create_common(const lbm_grid_desc *cells, int ncells, lbm_ctx **out) 
         cudaMemsetAsync(ctx->wall_acc, 0, sizeof(double) * 6 * ACC_COPIES * ncells, ctx->stream) != cudaSuccess ||
         cudaMemsetAsync(ctx->wall_last, 0, sizeof(double) * 6 * ncells, ctx->stream) != cudaSuccess ||
         cudaMemsetAsync(ctx->err, 0, 16, ctx->stream) != cudaSuccess ||
-        cudaMemsetAsync(ctx->gbar, 0, 16, ctx->stream) != cudaSuccess) {
+        cudaMemsetAsync(ctx->gbar, 0, 16, ctx->stream) != cudaSuccess ||
+        cudaMemsetAsync(ctx->stab_acc, 0, 64, ctx->stream) != cudaSuccess ||
+        cudaMemsetAsync(ctx->stab_accf, 0, 16, ctx->stream) != cudaSuccess) {
         lbm_destroy(ctx);
         return LBM_ERR_CUDA;
     }
@@ -1170,6 +1184,20 @@ lbm_status lbm_set_sweep_split(lbm_ctx *ctx, int enable) {
     ctx->split = enable != 0;
     drop_graph(ctx);
     return LBM_OK;
+}
+
+lbm_status lbm_set_momentum_stabilisation(lbm_ctx *ctx, int enable) {
+    if (!ctx) return LBM_ERR_ARG;
+    if (ctx->nlat != 1) return fail(ctx, LBM_ERR_UNSUPPORTED, "momentum stabilisation needs a single lattice");
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->stab = enable != 0;
+    ctx->lat_h[0].ubar = ctx->stab ? ctx->stab_acc + 4 : nullptr;
+    ctx->lat_h[0].ubarf = ctx->stab ? ctx->stab_accf : nullptr;
+    CK(cudaMemsetAsync(ctx->stab_acc, 0, 64, ctx->stream));
+    CK(cudaMemsetAsync(ctx->stab_accf, 0, 16, ctx->stream));
+    lbm_status st = upload_lattices(ctx);
+    drop_graph(ctx);
+    return st;
 }
 
 lbm_status lbm_set_remap_fused(lbm_ctx *ctx, int enable) {

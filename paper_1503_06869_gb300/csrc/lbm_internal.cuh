@@ -93,19 +93,25 @@ struct LatDev {
     // y walls (0 without them: no closure) and dynamic viscosity
     float cl_gamma, cl_mu;
     int off[Q];            // linear offset of x + c_q for cells off the periodic faces
+    // momentum stabilisation (Sec. 4.1): mean fluid velocity of the current
+    // step, subtracted from u in every equilibrium; null when off
+    const double *ubar;
+    const float *ubarf;
 };
 
 // Lattice parameters in the compute precision C (FP64 fields for double, the
 // FP32 copies otherwise).
 template <class C> struct LatPar {
-    C omega, omega_odd, rho0, inv_rho0, g[3], wlo[3], whi[3];
+    C omega, omega_odd, rho0, inv_rho0, g[3], wlo[3], whi[3], ubar[3];
     __device__ __forceinline__ explicit LatPar(const LatDev &L) {
         if constexpr (sizeof(C) == 8) {
             omega = L.omega; omega_odd = L.omega_odd; rho0 = L.rho0; inv_rho0 = L.inv_rho0;
             for (int k = 0; k < 3; ++k) { g[k] = L.g[k]; wlo[k] = L.wlo[k]; whi[k] = L.whi[k]; }
+            for (int k = 0; k < 3; ++k) ubar[k] = L.ubar ? L.ubar[k] : 0.0;
         } else {
             omega = L.fomega; omega_odd = L.fomega_odd; rho0 = L.frho0; inv_rho0 = L.finv_rho0;
             for (int k = 0; k < 3; ++k) { g[k] = L.fg[k]; wlo[k] = L.fwlo[k]; whi[k] = L.fwhi[k]; }
+            for (int k = 0; k < 3; ++k) ubar[k] = L.ubarf ? L.ubarf[k] : 0.0f;
         }
     }
 };
@@ -357,6 +363,12 @@ int remap_fused_max_blocks();
 int remap_fused_probe();
 cudaError_t launch_remap_fused(int prec, int next_parity, const RemapArgs &a, int blocks_per_body, int grid,
                                int mode, GridBar *bar, cudaStream_t s);
+// Momentum stabilisation (Sec. 4.1) of a single lattice: sum the
+// pre-collision velocity j / rho0 and the count of fluid cells into acc[0..3]
+// (the state the sweep of parity next_parity reads), then turn the sums into
+// the mean velocity (acc[4..6], FP32 copy in accf[0..2]) and clear them.
+cudaError_t launch_momentum_mean(int prec, int next_parity, const LatDev &h, const LatDev *d, const void *f,
+                                 const uint8_t *flags, double *acc, float *accf, cudaStream_t s);
 cudaError_t launch_clear_particles(const LatDev &h, const RemapArgs &a, int lat_index,
                                    cudaStream_t s);
 cudaError_t launch_claim_all(const RemapArgs &a, int blocks_per_body, cudaStream_t s);

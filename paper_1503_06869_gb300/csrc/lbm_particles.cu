@@ -824,6 +824,83 @@ __global__ void canonical_kernel(const LatDev *lat, const void *fv, const uint8_
     (void)pid;
 }
 
+// Momentum stabilisation (Sec. 4.1): per block, the sum over its fluid cells
+// of j = sum_q c_q f_q (offsets: sum_q c_q w_q rho0 = 0) as the coming sweep
+// reads the populations (AA layout of parity NEXT_ODD, a solid neighbour's
+// slot replaced by the cell's own, as in the export), and the number of fluid
+// cells; FP64 atomics into acc[0..3], one set per block.
+template <int PREC, int NEXT_ODD>
+__global__ void __launch_bounds__(256) momentum_sum_kernel(const LatDev *lat, const void *fv,
+                                                          const uint8_t *flags, double *acc) {
+    pdl_enter();
+    using S = Store<PREC>;
+    using T = typename S::T;
+    using C = typename S::C;
+    const LatDev &L = *lat;
+    const T *base = reinterpret_cast<const T *>(fv) + L.f_off;
+    const long long np = L.npad, co = L.c_off;
+    C sx = 0, sy = 0, sz = 0;
+    int cnt = 0;
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < L.n; x += gridDim.x * blockDim.x) {
+        const uint8_t fl = flags[co + x];
+        if (fl & F_SOLID) continue;
+        C jx = 0, jy = 0, jz = 0;
+        if (!NEXT_ODD) {
+#pragma unroll
+            for (int q = 1; q < Q; ++q) {
+                const C g = (C)S::ld(base + q * np + x);
+                if (cx(q)) jx += cx(q) > 0 ? g : -g;
+                if (cy(q)) jy += cy(q) > 0 ? g : -g;
+                if (cz(q)) jz += cz(q) > 0 ? g : -g;
+            }
+        } else {
+            const int yz = (int)L.divx.div((uint32_t)x), k = (int)L.divxy.div((uint32_t)x);
+            const int i = x - yz * L.nx, j = yz - k * L.ny;
+#pragma unroll
+            for (int q = 1; q < Q; ++q) {
+                const int z = lin(L, i - cx(q), j - cy(q), k - cz(q));
+                const bool own = fl != 0 && (flags[co + z] & F_SOLID);
+                const C g = (C)(own ? S::ld(base + q * np + x) : S::ld(base + opp(q) * np + z));
+                if (cx(q)) jx += cx(q) > 0 ? g : -g;
+                if (cy(q)) jy += cy(q) > 0 ? g : -g;
+                if (cz(q)) jz += cz(q) > 0 ? g : -g;
+            }
+        }
+        sx += jx;
+        sy += jy;
+        sz += jz;
+        ++cnt;
+    }
+    double v[4] = {(double)sx, (double)sy, (double)sz, (double)cnt};
+    __shared__ double part[8][4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) v[c] = warp_sum(v[c]);
+    if (lane == 0)
+        for (int c = 0; c < 4; ++c) part[warp][c] = v[c];
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w][threadIdx.x];
+        atomicAdd(acc + threadIdx.x, t);
+    }
+}
+
+// Mean velocity from the sums: ubar = sum j / (rho0 N_fluid) into acc[4..6]
+// and its FP32 copy; the sums are cleared for the next step.
+__global__ void momentum_mean_kernel(const LatDev *lat, double *acc, float *accf) {
+    pdl_enter();
+    const int k = threadIdx.x;
+    if (k >= 3) return;
+    const double n = acc[3];
+    const double u = n > 0.0 ? acc[k] / (lat->rho0 * n) : 0.0;
+    acc[4 + k] = u;
+    accf[k] = (float)u;
+    __syncwarp(0x7u);
+    acc[k] = 0.0;
+    if (k == 0) acc[3] = 0.0;
+}
+
 template <int PREC, int NEXT_ODD>
 __global__ void set_pdfs_kernel(const LatDev *lat, void *fv, const uint8_t *flags, const double *pdfs) {
     using S = Store<PREC>;
@@ -1122,6 +1199,28 @@ cudaError_t launch_remap_fused(int prec, int next_parity, const RemapArgs &a, in
     case LBM_BF16_OFFSET: return remap_fused_prec<LBM_BF16_OFFSET>(next_parity, a, bpb, grid, mode, bar, s);
     }
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_momentum_mean(int prec, int next_parity, const LatDev &h, const LatDev *d, const void *f,
+                                 const uint8_t *flags, double *acc, float *accf, cudaStream_t s) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long want = ((long long)h.n + 255) / 256;
+    const int grid = (int)(want < 4ll * sms ? want : 4ll * sms);
+    cudaError_t e = cudaErrorInvalidValue;
+#define LBM_MOMENTUM(P)                                                                              \
+    e = next_parity ? launch_pdl(momentum_sum_kernel<P, 1>, grid, 256, 0, s, d, f, flags, acc)        \
+                    : launch_pdl(momentum_sum_kernel<P, 0>, grid, 256, 0, s, d, f, flags, acc);
+    switch (prec) {
+    case LBM_F64: LBM_MOMENTUM(LBM_F64) break;
+    case LBM_F32: LBM_MOMENTUM(LBM_F32) break;
+    case LBM_F16_OFFSET: LBM_MOMENTUM(LBM_F16_OFFSET) break;
+    case LBM_BF16_OFFSET: LBM_MOMENTUM(LBM_BF16_OFFSET) break;
+    }
+#undef LBM_MOMENTUM
+    if (e != cudaSuccess) return e;
+    return launch_pdl(momentum_mean_kernel, 1, 32, 0, s, d, acc, accf);
 }
 
 // Full re-map for a new particle set, in three launches: clear the particle

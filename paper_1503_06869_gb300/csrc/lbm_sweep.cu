@@ -67,9 +67,11 @@ __device__ __forceinline__ int wrapc(int v, int n) { return v < 0 ? v + n : (v >
 // exit the post-collision offsets f~ - w rho0.  With dr = sum g = rho - rho0
 // the even equilibrium offset is w (dr - 1.5 rho0 u.u + 4.5 rho0 (c.u)^2),
 // the odd one 3 w rho0 c.u (Eq. EqPDF_TRT with c_s^2 = 1/3); the body force
-// enters as the odd source 3 w rho0 c.g.
+// enters as the odd source 3 w rho0 c.g.  Under momentum stabilisation
+// (Sec. 4.1) the equilibria are taken at u - ubar (ubar = 0 otherwise).
 template <class C>
-__device__ __forceinline__ void collide(C (&g)[Q], C om, C oo, C rho0, C inv, C gx, C gy, C gz) {
+__device__ __forceinline__ void collide(C (&g)[Q], C om, C oo, C rho0, C inv, C gx, C gy, C gz, C bx, C by,
+                                        C bz) {
     C dr = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
@@ -78,7 +80,7 @@ __device__ __forceinline__ void collide(C (&g)[Q], C om, C oo, C rho0, C inv, C 
         if (cy(q)) jy += cy(q) > 0 ? g[q] : -g[q];
         if (cz(q)) jz += cz(q) > 0 ? g[q] : -g[q];
     }
-    const C ux = jx * inv, uy = jy * inv, uz = jz * inv;
+    const C ux = jx * inv - bx, uy = jy * inv - by, uz = jz * inv - bz;
     const C base = dr - C(1.5) * rho0 * (ux * ux + uy * uy + uz * uz);
     g[0] = g[0] - om * (g[0] - C(wq(0)) * base);
 #pragma unroll
@@ -102,7 +104,8 @@ __device__ __forceinline__ void collide(C (&g)[Q], C om, C oo, C rho0, C inv, C 
 template <class C>
 __device__ __forceinline__ void collide_lat(C (&g)[Q], const LatDev &L) {
     const LatPar<C> p(L);
-    collide<C>(g, p.omega, p.omega_odd, p.rho0, p.inv_rho0, p.g[0], p.g[1], p.g[2]);
+    collide<C>(g, p.omega, p.omega_odd, p.rho0, p.inv_rho0, p.g[0], p.g[1], p.g[2], p.ubar[0], p.ubar[1],
+               p.ubar[2]);
 }
 
 struct CellGeom {

@@ -80,6 +80,7 @@ SIGNATURES = {
     "lbm_set_graphs": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_set_sweep_split": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_set_remap_fused": (C.c_int, [C.c_void_p, C.c_int]),
+    "lbm_set_momentum_stabilisation": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_set_sweep_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_get_sweep_timing": (C.c_int, [C.c_void_p, C.POINTER(C.c_double),
                                        C.POINTER(C.c_longlong)]),
@@ -239,6 +240,10 @@ def lbm_set_sweep_split(ctx, enable: bool):
 
 def lbm_set_remap_fused(ctx, enable: bool):
     _check(load().lbm_set_remap_fused(ctx, 1 if enable else 0), ctx)
+
+
+def lbm_set_momentum_stabilisation(ctx, enable: bool):
+    _check(load().lbm_set_momentum_stabilisation(ctx, 1 if enable else 0), ctx)
 
 
 def lbm_set_graphs(ctx, enable: bool):
@@ -444,6 +449,9 @@ class Simulation:
         structs = [particle_struct(p) for p in particles]
         lbm_set_particles(self.h, structs)
         self.np = len(structs)
+
+    def set_momentum_stabilisation(self, enable: bool = True):
+        lbm_set_momentum_stabilisation(self.h, enable)
 
     def step(self, n: int = 1):
         lbm_step(self.h, n)
