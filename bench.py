@@ -274,6 +274,9 @@ def main():
     ap.add_argument("--prec", default="f32", choices=["f64", "f32", "f16", "bf16"])
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--launch", type=int, default=None,
+                    help="fixed sweep block size (0 ring, -1 staged, 32..256 direct) instead of the autotuner's "
+                         "choice; for profiling runs, where the profiler's serialisation skews the autotuner")
     ap.add_argument("--remap-fused", action="store_true",
                     help="run the re-mapping step as one cooperative launch instead of five launches")
     args = ap.parse_args()
@@ -295,7 +298,10 @@ def main():
         lbm.lbm_set_closure(h, theta.astype(np.float16))
     if args.remap_fused:
         lbm.lbm_set_remap_fused(h, True)
-    lbm.lbm_autotune(h)
+    if args.launch is None:
+        lbm.lbm_autotune(h)
+    else:
+        lbm.lbm_set_launch(h, args.launch, 0)
     info = lbm.lbm_get_info(h)
     sim.step(args.warmup)
     sim.sync()
