@@ -143,7 +143,9 @@ def test_fibre_full_size_mapping_of_sampled_bodies(lbm):
         d = centres - centres[p]
         for a in (0, 2):  # periodic x and z: minimum image
             d[:, a] -= dims[a] * np.round(d[:, a] / dims[a])
-        for q in np.nonzero(np.linalg.norm(d, axis=1) <= reach + reach[p])[0]:  # ascending: lowest index wins
+        # every body that can reach into the box (its corners lie sqrt(3) reach from the centre); ascending
+        # order: the lowest index wins
+        for q in np.nonzero(np.linalg.norm(d, axis=1) <= np.sqrt(3.0) * reach[p] + reach)[0]:
             # cells that may lie inside body q: within b + 2 of its axis segment
             dq = cells - centres[q]
             for a in (0, 2):
