@@ -77,6 +77,8 @@ struct lbm_ctx {
     cudaGraphExec_t gexec = nullptr;
     bool gvalid = false;
     long long graph_launches = 0;   // kernels in one replay of the two-step graph
+    cudaGraphExec_t gexec1[2] = {nullptr, nullptr};  // one-step graphs, by parity of the step
+    long long graph1_launches[2] = {0, 0};
 
     bool timing = false;
     std::vector<cudaEvent_t> ev;
@@ -278,6 +280,10 @@ void drop_graph(lbm_ctx *ctx) {
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
     ctx->gexec = nullptr;
     ctx->gvalid = false;
+    for (int p = 0; p < 2; ++p) {
+        if (ctx->gexec1[p]) cudaGraphExecDestroy(ctx->gexec1[p]);
+        ctx->gexec1[p] = nullptr;
+    }
 }
 
 // One time step (Sec. 4.3): sweep at the parity of step t, rigid-body
@@ -367,6 +373,38 @@ lbm_status build_graph(lbm_ctx *ctx) {
         return fail(ctx, LBM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
     }
     ctx->gvalid = true;
+    return LBM_OK;
+}
+
+// One step through the captured graph of its parity (built on first use): a
+// caller that steps one at a time (and reads forces in between) pays one
+// graph launch per step instead of one launch per kernel.
+lbm_status graph_step(lbm_ctx *ctx) {
+    const int par = (int)(ctx->t & 1);
+    if (!ctx->gexec1[par]) {
+        cudaGraph_t g = nullptr;
+        const long long t0 = ctx->t, l0 = ctx->launches;
+        CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        const lbm_status s1 = enqueue_step(ctx, false);
+        cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+        ctx->t = t0;
+        ctx->graph1_launches[par] = ctx->launches - l0;
+        ctx->launches = l0;
+        if (s1 != LBM_OK) {
+            if (g) cudaGraphDestroy(g);
+            return s1;
+        }
+        if (e != cudaSuccess) return fail(ctx, LBM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&ctx->gexec1[par], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            ctx->gexec1[par] = nullptr;
+            return fail(ctx, LBM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        }
+    }
+    CK(cudaGraphLaunch(ctx->gexec1[par], ctx->stream));
+    ctx->t += 1;
+    ctx->launches += ctx->graph1_launches[par];
     return LBM_OK;
 }
 
@@ -822,9 +860,9 @@ lbm_status lbm_step(lbm_ctx *ctx, int nsteps) {
         return (moving && (ctx->t & 63) == 0) ? recount_tiles(ctx) : LBM_OK;
     };
     const bool use_graph = ctx->graphs && !ctx->timing && ctx->stream != nullptr;
-    if (use_graph && left >= 2) {
+    if (use_graph && left >= 1) {
         if (ctx->t & 1) {
-            lbm_status s = enqueue_step(ctx, false);
+            lbm_status s = graph_step(ctx);
             if (s == LBM_OK) s = maybe_recount();
             if (s != LBM_OK) return s;
             --left;
@@ -842,6 +880,12 @@ lbm_status lbm_step(lbm_ctx *ctx, int nsteps) {
                 lbm_status s = maybe_recount();
                 if (s != LBM_OK) return s;
             }
+        }
+        if (left == 1) {
+            lbm_status s = graph_step(ctx);
+            if (s == LBM_OK) s = maybe_recount();
+            if (s != LBM_OK) return s;
+            --left;
         }
     }
     while (left > 0) {

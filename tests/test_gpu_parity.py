@@ -290,6 +290,27 @@ def test_graph_replay_matches_eager(lbm):
     assert rel_l2(ua, ub, fa == 0) < 1e-13
 
 
+def test_single_step_graphs_match_eager(lbm):
+    """Steps taken one call at a time replay the one-step graph of their
+    parity; the state equals eager stepping and multi-step graph replay."""
+    w = small_shear(seed=4, n=24, steps=21)
+    sims = [lbm.Simulation(w.lattices[0], w.particles, prec="f64") for _ in range(3)]
+    lbm.lbm_set_graphs(sims[2].h, False)
+    for _ in range(21):
+        sims[0].step(1)
+    sims[1].step(3)
+    sims[1].step(18)
+    for _ in range(21):
+        sims[2].step(1)
+    ref = sims[2].fields()
+    for s in sims[:2]:
+        r, u, f, p, _ = s.fields()
+        assert np.array_equal(f, ref[2]) and np.array_equal(p, ref[3])
+        assert rel_l2(u, ref[1], ref[2] == 0) < 1e-13
+    n1 = lbm.lbm_get_launch_count(sims[0].h)
+    assert n1 == lbm.lbm_get_launch_count(sims[2].h)
+
+
 def test_autotune_keeps_state(lbm):
     lat = shear_lattice(40, 20, 18, 0.8, 0.02)
     g = lbm.Simulation(lat, [], prec="f32")
