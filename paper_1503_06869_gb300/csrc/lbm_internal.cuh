@@ -170,33 +170,44 @@ struct SweepArgs {
 };
 
 // Storage forms: every form holds g_q = f_q - w_q rho0 (the offset from rest).
-// Populations are touched once per step and the arrays are larger than L2, so
-// loads and stores carry the streaming (evict-first) cache hint
-// (ld.global.cs / st.global.cs): measured 4-5 % faster sweeps on GB300.
+// ld / st work on any address space (global, shared stage, local); ldg / stg
+// are for populations in global memory only: the sweep touches each once per
+// step and the arrays are larger than L2, so they carry the streaming
+// (evict-first) cache hint, ld.global.cs / st.global.cs (measured 4-5 %
+// faster sweeps on GB300).  A .global access on a shared or local address is
+// an invalid-address-space fault, so stage and register copies use ld / st.
 template <int PREC> struct Store;
 template <> struct Store<LBM_F64> {
     using T = double;
     using C = double;
-    static __device__ __forceinline__ C ld(const T *p) { return __ldcs(p); }
-    static __device__ __forceinline__ void st(T *p, C v) { __stcs(p, v); }
+    static __device__ __forceinline__ C ld(const T *p) { return *p; }
+    static __device__ __forceinline__ void st(T *p, C v) { *p = v; }
+    static __device__ __forceinline__ C ldg(const T *p) { return __ldcs(p); }
+    static __device__ __forceinline__ void stg(T *p, C v) { __stcs(p, v); }
 };
 template <> struct Store<LBM_F32> {
     using T = float;
     using C = float;
-    static __device__ __forceinline__ C ld(const T *p) { return __ldcs(p); }
-    static __device__ __forceinline__ void st(T *p, C v) { __stcs(p, v); }
+    static __device__ __forceinline__ C ld(const T *p) { return *p; }
+    static __device__ __forceinline__ void st(T *p, C v) { *p = v; }
+    static __device__ __forceinline__ C ldg(const T *p) { return __ldcs(p); }
+    static __device__ __forceinline__ void stg(T *p, C v) { __stcs(p, v); }
 };
 template <> struct Store<LBM_F16_OFFSET> {
     using T = __half;
     using C = float;
-    static __device__ __forceinline__ C ld(const T *p) { return __half2float(__ldcs(p)); }
-    static __device__ __forceinline__ void st(T *p, C v) { __stcs(p, __float2half_rn(v)); }
+    static __device__ __forceinline__ C ld(const T *p) { return __half2float(*p); }
+    static __device__ __forceinline__ void st(T *p, C v) { *p = __float2half_rn(v); }
+    static __device__ __forceinline__ C ldg(const T *p) { return __half2float(__ldcs(p)); }
+    static __device__ __forceinline__ void stg(T *p, C v) { __stcs(p, __float2half_rn(v)); }
 };
 template <> struct Store<LBM_BF16_OFFSET> {
     using T = __nv_bfloat16;
     using C = float;
-    static __device__ __forceinline__ C ld(const T *p) { return __bfloat162float(__ldcs(p)); }
-    static __device__ __forceinline__ void st(T *p, C v) { __stcs(p, __float2bfloat16_rn(v)); }
+    static __device__ __forceinline__ C ld(const T *p) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ void st(T *p, C v) { *p = __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ C ldg(const T *p) { return __bfloat162float(__ldcs(p)); }
+    static __device__ __forceinline__ void stg(T *p, C v) { __stcs(p, __float2bfloat16_rn(v)); }
 };
 
 

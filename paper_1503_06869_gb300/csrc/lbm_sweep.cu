@@ -370,8 +370,8 @@ __device__ __noinline__ void other_links(const SweepArgs &a, const LatDev &L, in
         nb += qz < 0 ? cg.dzm : (qz > 0 ? cg.dzp : 0);
         T *slot = base + qo * np + idx;
         const double v = bounce_link<PREC>(a, L, li, q, idx + nb, wrapc(cg.x + qx, L.nx), wrapc(cg.y + qy, L.ny),
-                                           wrapc(cg.z + qz, L.nz), (double)S::ld(slot), tkey, tval);
-        S::st(slot, (typename S::C)v);
+                                           wrapc(cg.z + qz, L.nz), (double)S::ldg(slot), tkey, tval);
+        S::stg(slot, (typename S::C)v);
     }
 }
 
@@ -475,7 +475,7 @@ __device__ __forceinline__ void near_cell(const SweepArgs &a, const LatDev &L, i
         if (ODD) {
 #pragma unroll
             for (int q = 0; q < Q; ++q)
-                if ((solid >> opp(q)) & 1u) g[q] = S::ld(base + q * np + idx);
+                if ((solid >> opp(q)) & 1u) g[q] = S::ldg(base + q * np + idx);
         }
     } else {
 #pragma unroll
@@ -484,15 +484,15 @@ __device__ __forceinline__ void near_cell(const SweepArgs &a, const LatDev &L, i
             if (!ODD) {
                 if (VIEW == 1) g[q] = S::ld(stage + q * Cfg::W + threadIdx.x);
                 else if (VIEW == 2) g[q] = ring_value<PREC>(col, q, idx & 1);
-                else g[q] = S::ld(base + q * np + idx);
+                else g[q] = S::ldg(base + q * np + idx);
             } else if ((solid >> p) & 1u) {
-                g[q] = S::ld(base + q * np + idx);
+                g[q] = S::ldg(base + q * np + idx);
             } else if (VIEW == 1) {
                 g[q] = S::ld(stage + q * Cfg::W + (L.off[p] & (Cfg::A - 1)) + threadIdx.x);
             } else if (VIEW == 2) {
                 g[q] = ring_value<PREC>(col, q, (idx + nb_off(cg, p)) & 1);
             } else {
-                g[q] = S::ld(base + p * np + idx + nb_off(cg, p));
+                g[q] = S::ldg(base + p * np + idx + nb_off(cg, p));
             }
         }
     }
@@ -530,9 +530,9 @@ __device__ __forceinline__ void near_cell(const SweepArgs &a, const LatDev &L, i
             if (cx(q)) sw[0] += cx(q) > 0 ? sm : -sm;
             if (cy(q)) sw[1] += cy(q) > 0 ? sm : -sm;
             if (cz(q)) sw[2] += cz(q) > 0 ? sm : -sm;
-            S::st(base + opp(q) * np + idx, g[q] - dbb);
+            S::stg(base + opp(q) * np + idx, g[q] - dbb);
         } else if ((wrest >> q) & 1u) {
-            S::st(base + opp(q) * np + idx, g[q]);
+            S::stg(base + opp(q) * np + idx, g[q]);
         } else if ((m0 >> q) & 1u) {
             // velocity bounce-back off body p0 (Eq. LBMMovWall): u_s at the
             // obstacle cell x_F + c_q, lever arm r_F + c_q
@@ -549,15 +549,15 @@ __device__ __forceinline__ void near_cell(const SweepArgs &a, const LatDev &L, i
             if (cx(q)) sb[0] += cx(q) > 0 ? sm : -sm;
             if (cy(q)) sb[1] += cy(q) > 0 ? sm : -sm;
             if (cz(q)) sb[2] += cz(q) > 0 ? sm : -sm;
-            S::st(base + opp(q) * np + idx, g[q] - dbb);
+            S::stg(base + opp(q) * np + idx, g[q] - dbb);
         } else if ((solid >> q) & 1u) {
             // another body (or the second moving wall layer): the unbounced
             // value goes to the bounce-back slot now, other_links rewrites it
-            S::st(base + opp(q) * np + idx, g[q]);
+            S::stg(base + opp(q) * np + idx, g[q]);
         } else if (!ODD) {
-            S::st(base + opp(q) * np + idx, g[q]);
+            S::stg(base + opp(q) * np + idx, g[q]);
         } else {
-            S::st(base + q * np + idx + nb_off(cg, q), g[q]);
+            S::stg(base + q * np + idx + nb_off(cg, q), g[q]);
         }
     }
     const uint32_t mo = solid & ~(m0 | wmain | wrest);
@@ -595,11 +595,11 @@ __device__ __noinline__ void wall_cell(const SweepArgs &a, const LatDev &L, int 
         cg = cell_geom(L, idx);
 #pragma unroll
         for (int q = 0; q < Q; ++q)
-            g[q] = (q != 0 && (SIDE == 0 ? cy(q) > 0 : cy(q) < 0)) ? S::ld(base + q * np + idx)
-                                                                  : S::ld(base + opp(q) * np + idx + nb_off(cg, opp(q)));
+            g[q] = (q != 0 && (SIDE == 0 ? cy(q) > 0 : cy(q) < 0)) ? S::ldg(base + q * np + idx)
+                                                                  : S::ldg(base + opp(q) * np + idx + nb_off(cg, opp(q)));
     } else {
 #pragma unroll
-        for (int q = 0; q < Q; ++q) g[q] = S::ld(base + q * np + idx);
+        for (int q = 0; q < Q; ++q) g[q] = S::ldg(base + q * np + idx);
     }
     collide_lat<C>(g, L);
     const LatPar<C> lp(L);
@@ -615,16 +615,16 @@ __device__ __noinline__ void wall_cell(const SweepArgs &a, const LatDev &L, int 
             cu += cy(q) > 0 ? u1 : -u1;
             if (cz(q)) cu += cz(q) > 0 ? u2 : -u2;
             const C dbb = C(6.0 * wq(q)) * rho0c * cu;
-            S::st(base + opp(q) * np + idx, g[q] - dbb);
+            S::stg(base + opp(q) * np + idx, g[q] - dbb);
             const C sm = C(2) * g[q] - dbb;
             if (cx(q)) sw[0] += cx(q) > 0 ? sm : -sm;
             sw[1] += cy(q) > 0 ? sm : -sm;
             if (cz(q)) sw[2] += cz(q) > 0 ? sm : -sm;
             mask |= 1u << q;
         } else if (!ODD) {
-            S::st(base + opp(q) * np + idx, g[q]);
+            S::stg(base + opp(q) * np + idx, g[q]);
         } else {
-            S::st(base + q * np + idx + nb_off(cg, q), g[q]);
+            S::stg(base + q * np + idx + nb_off(cg, q), g[q]);
         }
     }
     typename Acc<PREC>::V F[3];
@@ -646,17 +646,17 @@ __device__ __forceinline__ void bulk_cell(const SweepArgs &a, const LatDev &L, i
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         if (!ODD)
-            g[q] = S::ld(base + q * np + idx);
+            g[q] = S::ldg(base + q * np + idx);
         else
-            g[q] = S::ld(base + opp(q) * np + idx + nb_off(cg, opp(q)));
+            g[q] = S::ldg(base + opp(q) * np + idx + nb_off(cg, opp(q)));
     }
     collide_lat<C>(g, L);
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         if (!ODD)
-            S::st(base + opp(q) * np + idx, g[q]);
+            S::stg(base + opp(q) * np + idx, g[q]);
         else
-            S::st(base + q * np + idx + nb_off(cg, q), g[q]);
+            S::stg(base + q * np + idx + nb_off(cg, q), g[q]);
     }
 }
 
@@ -731,10 +731,10 @@ __global__ void __launch_bounds__(256, SweepBounds<PREC>::MINB)
         if (ODD) {
             cg = cell_geom(L, idx);
 #pragma unroll
-            for (int q = 0; q < Q; ++q) g[q] = S::ld(base + opp(q) * np + idx + nb_off(cg, opp(q)));
+            for (int q = 0; q < Q; ++q) g[q] = S::ldg(base + opp(q) * np + idx + nb_off(cg, opp(q)));
         } else {
 #pragma unroll
-            for (int q = 0; q < Q; ++q) g[q] = S::ld(base + q * np + idx);
+            for (int q = 0; q < Q; ++q) g[q] = S::ldg(base + q * np + idx);
         }
         const uint8_t fl = a.flags[L.c_off + idx];
         if (fl & F_SOLID) continue;
@@ -754,9 +754,9 @@ __global__ void __launch_bounds__(256, SweepBounds<PREC>::MINB)
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
             if (!ODD)
-                S::st(base + opp(q) * np + idx, g[q]);
+                S::stg(base + opp(q) * np + idx, g[q]);
             else
-                S::st(base + q * np + idx + nb_off(cg, q), g[q]);
+                S::stg(base + q * np + idx + nb_off(cg, q), g[q]);
         }
     }
     flush_forces<PREC>(a, tkey, tval);
@@ -864,9 +864,9 @@ __device__ __forceinline__ void bulk_cell_staged(const SweepArgs &a, const LatDe
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         if (!ODD)
-            S::st(base + opp(q) * np + idx, g[q]);
+            S::stg(base + opp(q) * np + idx, g[q]);
         else
-            S::st(base + q * np + idx + L.off[q], g[q]);
+            S::stg(base + q * np + idx + L.off[q], g[q]);
     }
 }
 
@@ -1092,9 +1092,9 @@ __global__ void __launch_bounds__(256, SweepBounds<PREC>::MINB)
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
             if (!ODD)
-                S::st(base + opp(q) * np + idx, g[q]);
+                S::stg(base + opp(q) * np + idx, g[q]);
             else
-                S::st(base + q * np + idx + nb_off(cg, q), g[q]);
+                S::stg(base + q * np + idx + nb_off(cg, q), g[q]);
         }
     }
     cp_async_wait<0>();
