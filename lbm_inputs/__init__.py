@@ -83,7 +83,9 @@ def axis_from_quat(q: Sequence[float]) -> Tuple[float, float, float]:
 
 @dataclass
 class Lattice:
-    """One shear cell: lattice size, relaxation, wall speeds (lattice units)."""
+    """One lattice: size, relaxation, periodic axes, wall speeds (lattice
+    units); free_slip[a] turns the wall layers of non-periodic axis a into
+    free-slip walls."""
     nx: int
     ny: int
     nz: int
@@ -94,6 +96,7 @@ class Lattice:
     wall_u_lo: Tuple[float, float, float] = (0.0, 0.0, 0.0)
     wall_u_hi: Tuple[float, float, float] = (0.0, 0.0, 0.0)
     body_force: Tuple[float, float, float] = (0.0, 0.0, 0.0)
+    free_slip: Tuple[int, int, int] = (0, 0, 0)
 
     @property
     def ncells(self) -> int:

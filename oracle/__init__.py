@@ -77,6 +77,7 @@ def _declare(lib):
     lib.orc_collide_cell.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_void_p,
                                      C.c_void_p, C.c_void_p]
     lib.orc_set_momentum_stabilisation.argtypes = [C.c_void_p, C.c_int]
+    lib.orc_set_free_slip.argtypes = [C.c_void_p, C.c_void_p]
     lib.orc_inside.restype = C.c_int
     lib.orc_inside.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int,
                                C.c_int, C.c_int]
@@ -196,6 +197,9 @@ class Sim:
                                     wh.ctypes.data_as(C.POINTER(C.c_double)),
                                     g.ctypes.data_as(C.POINTER(C.c_double)))
         self.np = 0
+        fs = np.array(getattr(lat, "free_slip", (0, 0, 0)), np.int32)
+        if fs.any():
+            self._L.orc_set_free_slip(self.h, _ptr(fs))
         if len(particles):
             self.set_particles(particles)
 

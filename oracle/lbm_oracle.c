@@ -80,6 +80,7 @@ struct orc_sim {
     long t;
     int stab;         /* momentum stabilisation on (Sec. 4.1) */
     double ubar[3];   /* mean fluid velocity of the current step */
+    int free_slip[3]; /* wall layers of a non-periodic axis reflect (Eq. FreeSlipBC) */
 };
 
 static int g_threads = 1;
@@ -427,6 +428,43 @@ static void obstacle_velocity(const orc_sim *s, uint32_t id, int i, int j, int k
     }
 }
 
+/* Index of the lattice direction (cx, cy, cz), -1 if none. */
+static int direction(int cx, int cy, int cz) {
+    for (int q = 0; q < Q; ++q)
+        if (CX[q] == cx && CY[q] == cy && CZ[q] == cz) return q;
+    return -1;
+}
+
+/* Free-slip wall (Eq. FreeSlipBC): the population f~_q leaving fluid cell
+   x_F = (i,j,k) into a wall cell is reflected at the wall, n the wall normal:
+   it arrives at x_F + c_q - n (n.c_q) with direction c_q - 2 n (n.c_q).  At an
+   edge or corner every wall layer the link crosses reflects its component.
+   Applies when every layer the link crosses belongs to a free-slip axis and
+   the arrival cell is fluid; returns 0 otherwise (the link bounces back).
+   No momentum is booked to the wall. */
+static int free_slip_link(orc_sim *s, int i, int j, int k, int q, double val) {
+    const int dims[3] = {s->nx, s->ny, s->nz}, at[3] = {i, j, k};
+    const int c[3] = {CX[q], CY[q], CZ[q]};
+    int d[3], r[3], crossed = 0;
+    for (int a = 0; a < 3; ++a) {
+        const int to = at[a] + c[a];
+        const int layer = !s->periodic[a] && c[a] != 0 && (to == 0 || to == dims[a] - 1);
+        if (layer && !s->free_slip[a]) return 0;
+        crossed |= layer;
+        d[a] = layer ? at[a] : wrap(to, dims[a]);
+        r[a] = layer ? -c[a] : c[a];
+    }
+    if (!crossed) return 0;
+    const long xd = cell_index(s, d[0], d[1], d[2]);
+    if (s->flag[xd] != FL_FLUID) return 0;
+    s->fnew[direction(r[0], r[1], r[2]) * s->n + xd] = val;
+    return 1;
+}
+
+void orc_set_free_slip(orc_sim *s, const int free_slip[3]) {
+    for (int a = 0; a < 3; ++a) s->free_slip[a] = free_slip[a] != 0 && !s->periodic[a];
+}
+
 /* Momentum stabilisation (Sec. 4.1): the mean velocity sum(c f)/rho0 over
    the fluid cells of the whole domain, taken before the collision of this
    step and subtracted from every cell's velocity in its equilibrium. */
@@ -484,6 +522,7 @@ static void collide_and_stream(orc_sim *s) {
                         s->fnew[q * n + xn] = ft[q];
                         continue;
                     }
+                    if (s->flag[xn] == FL_WALL && free_slip_link(s, i, j, k, q, ft[q])) continue;
                     /* velocity bounce-back (Eq. LBMMovWall) */
                     uint32_t id = s->pid[xn];
                     double us[3];

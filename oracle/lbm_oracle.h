@@ -57,6 +57,10 @@ void orc_set_threads(int nthreads);
 /* Momentum stabilisation (Sec. 4.1): each step's equilibria use u - ubar,
    ubar the mean velocity of all fluid cells before that step's collision. */
 void orc_set_momentum_stabilisation(orc_sim *s, int enable);
+/* Free-slip walls (Eq. FreeSlipBC) on the wall layers of each non-periodic
+   axis a with free_slip[a] != 0 (the moving-wall velocities of y are then
+   unused). */
+void orc_set_free_slip(orc_sim *s, const int free_slip[3]);
 
 /* building blocks, exposed for the pin tests */
 void orc_lattice(int *cx, int *cy, int *cz, double *w, int *opp);
