@@ -100,6 +100,17 @@ typedef struct lbm_grid_desc {
     void *(*dev_alloc)(size_t bytes, void *user); /* optional device allocator */
     void (*dev_free)(void *ptr, void *user);       /* its matching free */
     void *user;                /* passed to dev_alloc / dev_free */
+    int free_slip[3];          /* 1 = the wall layers of non-periodic axis x, y, z are
+                                * free-slip walls (Eq. FreeSlipBC: a population leaving a
+                                * fluid cell into the wall is reflected, its normal
+                                * component reversed; at edges every crossed layer
+                                * reflects).  Needs periodic[a] = 0; with free_slip[1]
+                                * the y wall speeds must be 0.  Bodies must keep off the
+                                * fluid layer next to a free-slip wall (lbm_set_particles
+                                * returns LBM_ERR_ARG, a step that moves a body there
+                                * LBM_ERR_UNSUPPORTED).  No momentum is booked to
+                                * free-slip walls (lbm_get_wall_forces covers the
+                                * no-slip y walls). */
 } lbm_grid_desc;
 
 /* One rigid body (Sec. 4.2-4.3).  shape LBM_SHAPE_ELLIPSOID: semi-axes

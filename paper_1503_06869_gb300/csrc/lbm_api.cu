@@ -158,6 +158,14 @@ lbm_status check_desc(const lbm_grid_desc *d, std::string &m) {
         if (!std::isfinite(d->body_force[a])) { m = "body force must be finite"; return LBM_ERR_ARG; }
     }
     if (storage_bytes(d->prec) == 0) { m = "unknown precision"; return LBM_ERR_ARG; }
+    for (int a = 0; a < 3; ++a)
+        if (d->free_slip[a] && d->periodic[a]) { m = "a free-slip axis cannot be periodic"; return LBM_ERR_ARG; }
+    if (d->free_slip[1])
+        for (int a = 0; a < 3; ++a)
+            if (d->wall_u_lo[a] != 0.0 || d->wall_u_hi[a] != 0.0) {
+                m = "free-slip y walls do not move";
+                return LBM_ERR_ARG;
+            }
     return LBM_OK;
 }
 
@@ -416,6 +424,10 @@ lbm_status check_err_word(lbm_ctx *ctx) {
         ctx->broken = true;
         return fail(ctx, LBM_ERR_NUMERIC, "non-finite force, torque or particle state");
     }
+    if (e & ERR_FSLIP_BODY) {
+        ctx->broken = true;
+        return fail(ctx, LBM_ERR_UNSUPPORTED, "a body reached the fluid layer next to a free-slip wall");
+    }
     if (e & ERR_TIMEOUT) {
         ctx->broken = true;
         return fail(ctx, LBM_ERR_TIMEOUT, "device-side wait ran out");
@@ -507,6 +519,9 @@ lbm_status create_common(const lbm_grid_desc *cells, int ncells, lbm_ctx **out) 
         L.px = d.periodic[0] ? 1 : 0;
         L.py = d.periodic[1] ? 1 : 0;
         L.pz = d.periodic[2] ? 1 : 0;
+        L.fsx = d.free_slip[0] ? 1 : 0;
+        L.fsy = d.free_slip[1] ? 1 : 0;
+        L.fsz = d.free_slip[2] ? 1 : 0;
         L.omega = 1.0 / d.tau;
         L.omega_odd = 1.0 / (d.magic / (d.tau - 0.5) + 0.5);
         L.rho0 = d.rho0;
@@ -683,6 +698,9 @@ lbm_status lbm_set_particles(lbm_ctx *ctx, const lbm_particle *p, int n) {
                              (capsule ? std::fabs(R[3 * a]) * (b.semi_axes[0] - b.semi_axes[1]) : 0.0);
             if (!per[a] && (b.pos[a] - h < 1.0 || b.pos[a] + h > dims[a] - 2.0))
                 return fail(ctx, LBM_ERR_ARG, "particle not inside the fluid region");
+            const int fsl = a == 0 ? Lt.fsx : (a == 1 ? Lt.fsy : Lt.fsz);
+            if (fsl && (b.pos[a] - h < 1.5 || b.pos[a] + h > dims[a] - 2.5))
+                return fail(ctx, LBM_ERR_ARG, "particle on the fluid layer next to a free-slip wall");
             if (per[a] && !(b.pos[a] >= 0.0 && b.pos[a] < dims[a]))
                 return fail(ctx, LBM_ERR_ARG, "periodic coordinate outside [0, n)");
             int lo = (int)std::floor(b.pos[a] - h) - 2, hi = (int)std::ceil(b.pos[a] + h) + 2;

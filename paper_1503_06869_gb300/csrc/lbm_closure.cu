@@ -161,7 +161,8 @@ __device__ void cell_velocity(const LatDev &L, const void *fv, const uint8_t *fl
         } else {
             const int zi = wrapi(i - cx(q), L.nx), zj = wrapi(j - cy(q), L.ny), zk = wrapi(k - cz(q), L.nz);
             const int z = zi + L.nx * (zj + L.ny * zk);
-            g = (flags[L.c_off + z] & F_SOLID) ? S::ld(base + q * np + x) : S::ld(base + opp(q) * np + z);
+            g = (flags[L.c_off + z] & (F_SOLID | F_FSLIP)) == F_SOLID ? S::ld(base + q * np + x)
+                                                                      : S::ld(base + opp(q) * np + z);
         }
         if (cx(q)) jx += cx(q) > 0 ? g : -g;
         if (cy(q)) jy += cy(q) > 0 ? g : -g;

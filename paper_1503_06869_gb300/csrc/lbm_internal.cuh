@@ -45,6 +45,9 @@ constexpr uint8_t F_WALL = 8;     // static wall layer (never re-mapped)
 // Fluid cells (with F_NEAR) whose wall/obstacle neighbours all belong to the
 // moving wall layer y = 0 (F_YLO) or y = ny-1 (F_YHI) of a non-periodic y
 // axis: their bounced directions are exactly those with c_y = -1 (resp. +1).
+// wall cell whose wall-layer axes are all free-slip: a link into it reflects
+// instead of bouncing back, and the odd step pulls through it like a fluid cell
+constexpr uint8_t F_FSLIP = 64;
 constexpr uint8_t F_YLO = 16;
 constexpr uint8_t F_YHI = 32;
 
@@ -78,7 +81,7 @@ struct LatDev {
     long long c_off;       // cell offset in the flag / id arenas
     FastDiv divx, divxy;   // idx -> (x, y, z)
     int px, py, pz;        // periodic flags
-    int pad0;
+    int fsx, fsy, fsz;     // free-slip wall layers (non-periodic axes only)
     double omega, omega_odd, rho0;
     double inv_rho0;       // 1 / rho0
     double rho18;          // rho0 / 18: 2 w_q rho0 = (36 w_q) rho0 / 18 with 36 w_q in {1, 2}
@@ -294,6 +297,7 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
 // Device error-word bits.
 constexpr uint32_t ERR_NONFINITE = 1u;
 constexpr uint32_t ERR_TIMEOUT = 2u;
+constexpr uint32_t ERR_FSLIP_BODY = 4u;  // a body reached the fluid layer next to a free-slip wall
 
 // --- launchers (defined in the .cu files) ---------------------------------
 // Sweep variants: direct (one cell per thread, `block` threads per block),

@@ -25,7 +25,10 @@
 // with both cells fluid A holds f_p(z) and B holds f_opp(p)(z'); with only z
 // fluid B holds f_p(z); with only z' fluid A holds f_opp(p)(z').  When a status
 // changes, pass C reads the link's logical values under the old statuses and
-// rewrites them under the new ones.
+// rewrites them under the new ones.  A free-slip wall cell (F_FSLIP) is not a
+// bounce-back neighbour: the odd sweep pulls through its slots, which carry
+// the values reflected at the wall (see the sweep); bodies keep off the fluid
+// layer next to such walls, so pass C never meets one.
 #include "lbm_internal.cuh"
 
 namespace lbm {
@@ -327,6 +330,9 @@ __device__ void rigid_unit(const RemapArgs &a, int warp, int lane) {
     // re-mapping box along k: union of the old and new bounding boxes plus a
     // margin of two cells, in FP32 with a slack far above its rounding
     const float posf = c.hi, coldf = (float)pos;
+    // a body must keep off the fluid layer next to a free-slip wall
+    const int fsk = k == 0 ? Lt.fsx : (k == 1 ? Lt.fsy : Lt.fsz);
+    if (fsk && (posf - hnew < 1.5f || posf + hnew > (float)dim - 2.5f)) atomicOr(a.err, ERR_FSLIP_BODY);
     float lo = fminf(coldf - hold, posf - hnew) - 1e-3f;
     float hi = fmaxf(coldf + hold, posf + hnew) + 1e-3f;
     // a wrapped centre makes the two boxes an image apart: use the new one
@@ -553,20 +559,38 @@ __global__ void fixup_region_kernel(RemapArgs a, int bpb) {
     fixup_region<PREC, NEXT_ODD>(a, blockIdx.x, bpb);
 }
 
+// Wall cell (i,j,k) all of whose wall layers are free-slip walls.
+__device__ __forceinline__ bool free_slip_cell(const LatDev &L, int i, int j, int k) {
+    const bool lx = !L.px && (i == 0 || i == L.nx - 1);
+    const bool ly = !L.py && (j == 0 || j == L.ny - 1);
+    const bool lz = !L.pz && (k == 0 || k == L.nz - 1);
+    return (lx || ly || lz) && (!lx || L.fsx) && (!ly || L.fsy) && (!lz || L.fsz);
+}
+
 // Flag byte of cell (i,j,k) from the particle-id map, and for a fluid cell
-// its link word (LK_* layout) and the first body among its neighbours.
+// its link word (LK_* layout) and the first body among its neighbours.  A
+// link into a free-slip wall cell sets the wall bit only (not the solid bit):
+// it reflects, and the odd step pulls through it.
 __device__ __forceinline__ uint8_t flag_of(const LatDev &L, const uint32_t *pid, long long coff, int i,
                                            int j, int k, uint64_t &links, uint32_t &p0) {
     links = 0;
     p0 = PID_FLUID;
     const uint32_t id = pid[coff + i + L.nx * (j + L.ny * k)];
-    if (id != PID_FLUID) return id >= PID_WALL ? (F_SOLID | F_WALL) : F_SOLID;
+    if (id != PID_FLUID)
+        return id >= PID_WALL ? (F_SOLID | F_WALL | (free_slip_cell(L, i, j, k) ? F_FSLIP : 0)) : F_SOLID;
     bool near = false, only_lo = true, only_hi = true;
     uint32_t solid = 0, wall = 0, body = 0;
 #pragma unroll
     for (int q = 1; q < Q; ++q) {
         const int n = lin(L, i + cx(q), j + cy(q), k + cz(q));
         const uint32_t nid = pid[coff + n];
+        if (nid >= PID_WALL && nid != PID_FLUID &&
+            free_slip_cell(L, wrapc(i + cx(q), L.nx), wrapc(j + cy(q), L.ny), wrapc(k + cz(q), L.nz))) {
+            wall |= 1u << q;
+            near = true;
+            only_lo = only_hi = false;
+            continue;
+        }
         if (nid != PID_FLUID) {
             solid |= 1u << q;
             if (nid >= PID_WALL) {
@@ -804,7 +828,7 @@ __global__ void canonical_kernel(const LatDev *lat, const void *fv, const uint8_
             g = (double)S::ld(base + q * np + x);
         } else {
             const int z = lin(L, i - cx(q), j - cy(q), k - cz(q));
-            if (flags[co + z] & F_SOLID)
+            if ((flags[co + z] & (F_SOLID | F_FSLIP)) == F_SOLID)
                 g = (double)S::ld(base + q * np + x);
             else
                 g = (double)S::ld(base + opp(q) * np + z);
@@ -859,7 +883,7 @@ __global__ void __launch_bounds__(256) momentum_sum_kernel(const LatDev *lat, co
 #pragma unroll
             for (int q = 1; q < Q; ++q) {
                 const int z = lin(L, i - cx(q), j - cy(q), k - cz(q));
-                const bool own = fl != 0 && (flags[co + z] & F_SOLID);
+                const bool own = fl != 0 && (flags[co + z] & (F_SOLID | F_FSLIP)) == F_SOLID;
                 const C g = (C)(own ? S::ld(base + q * np + x) : S::ld(base + opp(q) * np + z));
                 if (cx(q)) jx += cx(q) > 0 ? g : -g;
                 if (cy(q)) jy += cy(q) > 0 ? g : -g;
@@ -920,7 +944,7 @@ __global__ void set_pdfs_kernel(const LatDev *lat, void *fv, const uint8_t *flag
             S::st(base + q * np + x, (typename S::C)g);
         } else {
             const int z = lin(L, i - cx(q), j - cy(q), k - cz(q));
-            if (flags[co + z] & F_SOLID)
+            if ((flags[co + z] & (F_SOLID | F_FSLIP)) == F_SOLID)
                 S::st(base + q * np + x, (typename S::C)g);
             else
                 S::st(base + opp(q) * np + z, (typename S::C)g);

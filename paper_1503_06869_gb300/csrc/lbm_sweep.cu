@@ -37,6 +37,9 @@ constexpr uint32_t KEY_WALL = 0x80000000u;
 __constant__ int c_cx[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
 __constant__ int c_cy[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
 __constant__ int c_cz[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+// direction index of (cx, cy, cz) at (cx + 1) + 3 (cy + 1) + 9 (cz + 1); -1: none
+__constant__ int c_qidx[27] = {-1, 16, -1, 12, 6, 13, -1, 17, -1, 8, 4, 9, 2, 0, 1, 10, 3, 7,
+                               -1, 18, -1, 14, 5, 11, -1, 15, -1};
 __constant__ double c_w[Q] = {1.0 / 3.0, 1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0,
                               1.0 / 18.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0,
                               1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0,
@@ -448,6 +451,8 @@ __device__ __forceinline__ void near_cell(const SweepArgs &a, const LatDev &L, i
     const uint32_t solid = (uint32_t)lk & LK_MASK;            // bit q: x + c_q is a wall or obstacle cell
     const uint32_t wall = (uint32_t)(lk >> LK_WALL) & LK_MASK;  // bit q: x + c_q is a wall-layer cell
     const uint32_t m0 = (uint32_t)(lk >> LK_BODY) & LK_MASK;    // bit q: x + c_q is a cell of body p0
+    // free-slip wall links carry the wall bit without the solid bit
+    const uint32_t fsl = wall & ~solid, wbb = wall & solid;
     // Obstacle links: the first body met (p0) has its motion loaded once and
     // its links are bounced inline in the compute precision, their momentum
     // summed per cell; links to any further body take bounce_link.
@@ -503,17 +508,17 @@ __device__ __forceinline__ void near_cell(const SweepArgs &a, const LatDev &L, i
     // both moving layers (ny = 3) sends the second layer's links through
     // bounce_link.
     uint32_t wlo = 0, whi = 0;
-    if (wall && !L.py) {
+    if (wbb && !L.py) {
 #pragma unroll
         for (int q = 1; q < Q; ++q)
-            if ((wall >> q) & 1u) {
+            if ((wbb >> q) & 1u) {
                 if (cg.y + cy(q) == 0) wlo |= 1u << q;
                 else if (cg.y + cy(q) == L.ny - 1) whi |= 1u << q;
             }
     }
     const int wside = wlo ? 0 : (whi ? 1 : -1);
     const uint32_t wmain = wlo ? wlo : whi;
-    const uint32_t wrest = wall & ~(wlo | whi);
+    const uint32_t wrest = wbb & ~(wlo | whi);
     const LatPar<C> lp(L);
     const C rho0c = lp.rho0;
     const C *uw = wside == 1 ? lp.whi : lp.wlo;
@@ -554,6 +559,27 @@ __device__ __forceinline__ void near_cell(const SweepArgs &a, const LatDev &L, i
             // another body (or the second moving wall layer): the unbounced
             // value goes to the bounce-back slot now, other_links rewrites it
             S::stg(base + opp(q) * np + idx, g[q]);
+        } else if ((fsl >> q) & 1u) {
+            // free-slip wall (Eq. FreeSlipBC): the components whose wall layer
+            // the link crosses are reversed; the value arrives at x + c_q minus
+            // those components, in the reflected direction r
+            const bool ax = cx(q) != 0 && !L.px && (cg.x + cx(q) == 0 || cg.x + cx(q) == L.nx - 1);
+            const bool ay = cy(q) != 0 && !L.py && (cg.y + cy(q) == 0 || cg.y + cy(q) == L.ny - 1);
+            const bool az = cz(q) != 0 && !L.pz && (cg.z + cz(q) == 0 || cg.z + cz(q) == L.nz - 1);
+            const int r = c_qidx[(ax ? -cx(q) : cx(q)) + 1 + 3 * ((ay ? -cy(q) : cy(q)) + 1) +
+                                 9 * ((az ? -cz(q) : cz(q)) + 1)];
+            if (!ODD) {
+                // the arrival cell pulls it next step through the wall cell
+                // x + (crossed components of c_q), whose slots are otherwise unused
+                const int wcell = idx + (ax ? cx(q) : 0) + (ay ? cy(q) * L.nx : 0) + (az ? cz(q) * L.nx * L.ny : 0);
+                S::stg(base + (long long)opp(r) * np + wcell, g[q]);
+            } else {
+                int off = 0;
+                if (cx(q) && !ax) off += cx(q) > 0 ? cg.dxp : cg.dxm;
+                if (cy(q) && !ay) off += cy(q) > 0 ? cg.dyp : cg.dym;
+                if (cz(q) && !az) off += cz(q) > 0 ? cg.dzp : cg.dzm;
+                S::stg(base + (long long)r * np + idx + off, g[q]);
+            }
         } else if (!ODD) {
             S::stg(base + opp(q) * np + idx, g[q]);
         } else {

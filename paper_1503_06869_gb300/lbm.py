@@ -39,7 +39,8 @@ class lbm_grid_desc(C.Structure):
                 ("wall_u_lo", D3), ("wall_u_hi", D3), ("body_force", D3),
                 ("prec", C.c_int),
                 ("cuda_stream", C.c_void_p),
-                ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("user", C.c_void_p)]
+                ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("user", C.c_void_p),
+                ("free_slip", C.c_int * 3)]
 
 
 class lbm_particle(C.Structure):
@@ -366,6 +367,7 @@ def grid_desc(lat, prec: int = LBM_F32, stream_handle: int = 0,
         d.wall_u_lo[a] = lat.wall_u_lo[a]
         d.wall_u_hi[a] = lat.wall_u_hi[a]
         d.body_force[a] = lat.body_force[a]
+        d.free_slip[a] = int(getattr(lat, "free_slip", (0, 0, 0))[a])
     d.prec = prec
     d.cuda_stream = stream_handle or None
     if memory is not None:
