@@ -38,6 +38,7 @@ struct lbm_ctx {
     uint32_t *pid = nullptr, *pid_prev = nullptr;
     double *wall_acc = nullptr, *wall_last = nullptr;
     uint32_t *tbits = nullptr;      // direct sweep: tiles that may hold non-bulk cells
+    int *tile_lat = nullptr;        // batches: lattice of every sweep tile
     uint64_t *links = nullptr;      // per-cell link words (neighbour masks)
     uint32_t *nbody = nullptr;      // per-cell first neighbouring body
     uint32_t *near_list = nullptr;  // split direct sweep: compacted near-obstacle cells
@@ -206,6 +207,7 @@ SweepArgs sweep_args(lbm_ctx *ctx) {
     a.wall_acc = ctx->wall_acc;
     a.err = ctx->err;
     a.tbits = ctx->variant == SWEEP_DIRECT ? ctx->tbits : nullptr;
+    a.tile_lat = ctx->tile_lat;
     a.links = ctx->links;
     a.nbody = ctx->nbody;
     const bool split = ctx->split && ctx->variant == SWEEP_DIRECT;
@@ -280,6 +282,7 @@ lbm_status recount_tiles(lbm_ctx *ctx) {
 lbm_status upload_lattices(lbm_ctx *ctx) {
     CK(cudaMemcpyAsync(ctx->lat_d, ctx->lat_h.data(), sizeof(LatDev) * ctx->nlat, cudaMemcpyHostToDevice,
                        ctx->stream));
+    if (ctx->tile_lat) CK(launch_tile_map(ctx->lat_d, ctx->nlat, ctx->ntiles, ctx->tile_lat, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return LBM_OK;
 }
@@ -579,10 +582,11 @@ lbm_status create_common(const lbm_grid_desc *cells, int ncells, lbm_ctx **out) 
         long long tiles32 = 0;  // tiles of the smallest direct-sweep tile (32 cells)
         for (auto &L : ctx->lat_h) tiles32 += (L.n + 31) / 32;
         ctx->tbits = (uint32_t *)owned_alloc(ctx, sizeof(uint32_t) * (size_t)(tiles32 / 32 + 1));
+        if (ncells > 1) ctx->tile_lat = (int *)owned_alloc(ctx, sizeof(int) * (size_t)(tiles32 + 1));
     }
     if (!ctx->lat_d || !ctx->f || !ctx->flags || !ctx->pid || !ctx->pid_prev || !ctx->wall_acc ||
         !ctx->wall_last || !ctx->err || !ctx->tbits || !ctx->links || !ctx->nbody || !ctx->near_list ||
-        !ctx->near_count || !ctx->gbar || !ctx->stab_acc || !ctx->stab_accf) {
+        !ctx->near_count || !ctx->gbar || !ctx->stab_acc || !ctx->stab_accf || (ncells > 1 && !ctx->tile_lat)) {
         lbm_destroy(ctx);
         return LBM_ERR_OOM;
     }

@@ -170,6 +170,7 @@ struct SweepArgs {
     // updates them with every lane busy
     uint32_t *near_list;
     uint32_t *near_count;
+    const int *tile_lat;     // batches: lattice of every tile (null: binary search on tile0)
 };
 
 // Storage forms: every form holds g_q = f_q - w_q rho0 (the offset from rest).
@@ -308,6 +309,8 @@ constexpr int SWEEP_STAGED = 1;
 constexpr int SWEEP_RING = 2;
 cudaError_t launch_sweep(int prec, int parity, int variant, const SweepArgs &a, int grid, int block,
                          cudaStream_t s);
+// Fill map[t] = lattice of tile t for the current tile size (lat: device table).
+cudaError_t launch_tile_map(const LatDev *lat, int nlat, int ntiles, int *map, cudaStream_t s);
 
 // Learned closure (see lbm_closure.cu): features of every body, network
 // inference (applied to the bodies' accumulators, or written out), training.

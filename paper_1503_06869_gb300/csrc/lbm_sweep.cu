@@ -149,6 +149,7 @@ __device__ __forceinline__ CellGeom cell_geom(const LatDev &L, int idx) {
 template <bool SINGLE>
 __device__ __forceinline__ int tile_lattice(const SweepArgs &a, int tile) {
     if (SINGLE) return 0;
+    if (a.tile_lat) return a.tile_lat[tile];
     int lo = 0, hi = a.nlat - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -848,15 +849,7 @@ __device__ __forceinline__ void issue_tile(const SweepArgs &a, int tile, typenam
                                            uint64_t *bar) {
     using Cfg = StageCfg<PREC>;
     using T = typename Store<PREC>::T;
-    int li = 0;
-    if (!SINGLE) {
-        int lo = 0, hi = a.nlat - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (a.lat[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
-        }
-        li = lo;
-    }
+    const int li = tile_lattice<SINGLE>(a, tile);
     const LatDev &L = SINGLE ? a.lat0 : a.lat[li];
     const long long idx0 = (long long)(tile - L.tile0) * Cfg::TILE;
     const T *f = reinterpret_cast<const T *>(a.f) + L.f_off;
@@ -938,15 +931,7 @@ __global__ void __launch_bounds__(256, SweepBounds<PREC>::MINB)
         const bool ok = mbar_wait_bounded(&bars[s], (uint32_t)((k / Cfg::S) & 1));
         if (ok) {
             const int tile = blockIdx.x + k * gridDim.x;
-            int li = 0;
-            if (!SINGLE) {
-                int lo = 0, hi = a.nlat - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (a.lat[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
-                }
-                li = lo;
-            }
+            const int li = tile_lattice<SINGLE>(a, tile);
             const LatDev &L = SINGLE ? a.lat0 : a.lat[li];
             const int idx = (tile - L.tile0) * Cfg::TILE + tid;
             const T *stage = stages + s * Cfg::STAGE_ELEMS;
@@ -1262,7 +1247,27 @@ int max_blocks_prec(int variant, int block) {
     return nb;
 }
 
+// Lattice of every sweep tile (batches): tiles are numbered lattice by
+// lattice, lattice l owning [tile0_l, tile0_{l+1}); one binary search per tile
+// here instead of one per block in every sweep.
+__global__ void tile_map_kernel(const LatDev *lat, int nlat, int ntiles, int *map) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    int lo = 0, hi = nlat - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (lat[mid].tile0 <= t) lo = mid; else hi = mid - 1;
+    }
+    map[t] = lo;
+}
+
 }  // namespace
+
+cudaError_t launch_tile_map(const LatDev *lat, int nlat, int ntiles, int *map, cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
+    tile_map_kernel<<<(ntiles + 255) / 256, 256, 0, s>>>(lat, nlat, ntiles, map);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_sweep(int prec, int parity, int variant, const SweepArgs &a, int grid, int block,
                          cudaStream_t s) {
