@@ -821,6 +821,7 @@ lbm_status lbm_set_particles(lbm_ctx *ctx, const lbm_particle *p, int n) {
     P.acc = part_alloc<double>(ctx, 6 * ACC_COPIES * m);
     P.last = part_alloc<double>(ctx, 6 * m);
     P.region = part_alloc<int>(ctx, 6 * m);
+    P.changed = part_alloc<int>(ctx, m);
     for (void *b : ctx->part_bufs)
         if (!b) {
             free_particles(ctx);
@@ -856,6 +857,7 @@ lbm_status lbm_set_particles(lbm_ctx *ctx, const lbm_particle *p, int n) {
     CK(up(P.region, region.data(), 4 * region.size()));
     CK(cudaMemsetAsync(P.acc, 0, sizeof(double) * 6 * ACC_COPIES * m, ctx->stream));
     CK(cudaMemsetAsync(P.last, 0, sizeof(double) * 6 * m, ctx->stream));
+    CK(cudaMemsetAsync(P.changed, 0, sizeof(int) * m, ctx->stream));
     // full re-map of every lattice for the next sweep's parity
     RemapArgs ra = remap_args(ctx);
     const int next_odd = (int)(ctx->t & 1);

@@ -135,6 +135,7 @@ struct PartDev {
     double *acc;       // 6 per body: hydrodynamic F, M summed by the sweep
     double *last;      // 6 per body: F, M of the last completed step
     int *region;       // 6 per body: lo[3], ext[3] of the re-mapping box
+    int *changed;      // per body: this step's uncover / claim changed a cell's owner (fix-up and flags run)
 };
 
 // FP32 copy of a body's pose and motion (PartDev::bodyf, BF_STRIDE floats per

@@ -204,6 +204,7 @@ __device__ void rigid_unit(const RemapArgs &a, int warp, int lane) {
         return;
     }
     const size_t t = (size_t)warp;
+    if (lane == 0) P.changed[t] = 0;  // set again by this step's uncover / claim passes
     const int k = lane < 3 ? lane : 0;  // vector component of this lane (lanes >= 3 mirror 0, store nothing)
     const bool vec = lane < 3;
     // ---- loads
@@ -419,11 +420,15 @@ __device__ void remap_region(const RemapArgs &a, int unit, int bpb) {
                 a.pid[cg] = PID_FLUID;
                 a.pid_prev[cg] = (uint32_t)p;
                 a.flags[cg] |= F_CHANGED;
+                P.changed[p] = 1;
             }
         } else {  // claim
             if (!(a.flags[cg] & F_WALL) && inside_fast(L, pos, R64, semi, bf, c.i, c.j, c.k)) {
                 const uint32_t old = atomicMin(&a.pid[cg], (uint32_t)p);
                 if (old == PID_FLUID) a.flags[cg] |= F_CHANGED;
+                // a new obstacle cell, or one taken from a higher-index body
+                // (the neighbours' first-body links change)
+                if (old > (uint32_t)p) P.changed[p] = 1;
             }
         }
     }
@@ -534,6 +539,9 @@ __device__ void fixup_region(const RemapArgs &a, int unit, int bpb) {
     const int p = rl.p;
     const PartDev &P = a.P;
     if (p >= P.np) return;
+    // every changed cell and its neighbours lie in the box of the body that
+    // changed it: a body that changed nothing has nothing to fix up here
+    if (!P.changed[p]) return;
     const int *reg = P.region + 6 * p;
     const int vol = reg[3] * reg[4] * reg[5];
     const LatDev &L = a.lat[P.cell[p]];
@@ -621,6 +629,7 @@ __device__ void flags_region(const RemapArgs &a, int unit, int bpb) {
     const int p = rl.p;
     const PartDev &P = a.P;
     if (p >= P.np) return;
+    if (!P.changed[p]) return;  // no owner changed in this box: flags and links stand
     const int *reg = P.region + 6 * p;
     const int vol = reg[3] * reg[4] * reg[5];
     const LatDev &L = a.lat[P.cell[p]];
