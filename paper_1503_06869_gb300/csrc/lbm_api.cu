@@ -52,6 +52,7 @@ struct lbm_ctx {
     PartDev P{};
     std::vector<void *> part_bufs;
     std::vector<int> shape_h;       // per body: LBM_SHAPE_*
+    double *host_stage = nullptr;   // pinned: last F, M of every body (6 per body), then the error word
     std::vector<double> density_h;  // per body: density as given
 
     void *f_arena = nullptr;        // population allocation: guard | planes | guard
@@ -419,10 +420,7 @@ lbm_status graph_step(lbm_ctx *ctx) {
     return LBM_OK;
 }
 
-lbm_status check_err_word(lbm_ctx *ctx) {
-    uint32_t e = 0;
-    CK(cudaMemcpyAsync(&e, ctx->err, sizeof(e), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
+lbm_status eval_err_word(lbm_ctx *ctx, uint32_t e) {
     if (e & ERR_NONFINITE) {
         ctx->broken = true;
         return fail(ctx, LBM_ERR_NUMERIC, "non-finite force, torque or particle state");
@@ -436,6 +434,13 @@ lbm_status check_err_word(lbm_ctx *ctx) {
         return fail(ctx, LBM_ERR_TIMEOUT, "device-side wait ran out");
     }
     return LBM_OK;
+}
+
+lbm_status check_err_word(lbm_ctx *ctx) {
+    uint32_t e = 0;
+    CK(cudaMemcpyAsync(&e, ctx->err, sizeof(e), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return eval_err_word(ctx, e);
 }
 
 void free_particles(lbm_ctx *ctx) {
@@ -643,6 +648,7 @@ lbm_status lbm_destroy(lbm_ctx *ctx) {
     drop_graph(ctx);
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
     for (void *p : ctx->owned) dfree(ctx, p);
+    if (ctx->host_stage) cudaFreeHost(ctx->host_stage);
     delete ctx;
     return LBM_OK;
 }
@@ -828,6 +834,9 @@ lbm_status lbm_set_particles(lbm_ctx *ctx, const lbm_particle *p, int n) {
             return fail(ctx, LBM_ERR_OOM, "particle buffers");
         }
     ctx->np = n;
+    if (ctx->host_stage) cudaFreeHost(ctx->host_stage);
+    ctx->host_stage = nullptr;
+    CK(cudaMallocHost((void **)&ctx->host_stage, sizeof(double) * (6 * m + 2)));
     ctx->shape_h = shape;
     ctx->density_h = density;
     auto up = [&](void *dst, const void *src, size_t bytes) -> cudaError_t {
@@ -932,15 +941,18 @@ lbm_status lbm_get_forces(lbm_ctx *ctx, double *force3n, double *torque3n, int n
     if (!ctx) return LBM_ERR_ARG;
     if (n < 0 || n > ctx->np) return fail(ctx, LBM_ERR_ARG, "n out of range");
     if (n == 0) return LBM_OK;
-    std::vector<double> buf(6 * (size_t)n);
-    CK(cudaMemcpyAsync(buf.data(), ctx->P.last, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, ctx->stream));
+    // forces and the error word into pinned memory, one synchronisation
+    double *buf = ctx->host_stage;
+    uint32_t *err = reinterpret_cast<uint32_t *>(buf + 6 * (size_t)ctx->np);
+    CK(cudaMemcpyAsync(buf, ctx->P.last, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(err, ctx->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     for (int i = 0; i < n; ++i)
         for (int a = 0; a < 3; ++a) {
             if (force3n) force3n[3 * i + a] = buf[6 * i + a];
             if (torque3n) torque3n[3 * i + a] = buf[6 * i + 3 + a];
         }
-    return check_err_word(ctx);
+    return eval_err_word(ctx, *err);
 }
 
 lbm_status lbm_get_wall_forces(lbm_ctx *ctx, int cell, double *f6) {
