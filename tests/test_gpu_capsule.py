@@ -13,7 +13,7 @@ velocity over the last half of the run (sampled every 200 steps) is compared
 with the paper's LBM result omega*_LBM; the band is the paper's own spread
 delta_omega = (max - min) / mean of its samples (at least 3 %).  The paper used
 an 816^3 cube and reports the wall influence on rotation as negligible; the
-cubes here are 6-8 body lengths wide.  It also checks that omega lies between
+cubes here are 4-7 body lengths wide.  It also checks that omega lies between
 Tirado's cylinders with and without the end caps, as the paper finds.
 """
 import json
@@ -130,7 +130,8 @@ def test_rejects_inconsistent_spherocylinder(lbm):
 # rotational validation against the paper's LBM angular velocities
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("aspect,box,steps", [(4, 112, 24000), (8, 160, 40000), (14, 224, 60000)])
+@pytest.mark.parametrize("aspect,box,steps", [(4, 112, 24000), (6, 136, 32000), (8, 160, 40000), (10, 192, 50000),
+                                              (12, 208, 56000), (14, 224, 60000)])
 def test_rotational_validation_against_table_A(lbm, aspect, box, steps):
     gold = json.load(open(os.path.join(HERE, "golden", "table_A_tirado.json")))
     col = gold["inverse_eps"].index(aspect)
