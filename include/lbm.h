@@ -157,8 +157,10 @@ lbm_status lbm_create_batch(const lbm_grid_desc *cells, int ncells, lbm_ctx **ou
  * Particle cells that become fluid are refilled with f^eq(rho0, 0); cells that
  * become obstacles drop their populations.  n = 0 removes all particles.
  * Errors: LBM_ERR_ARG for n < 0, p == NULL with n > 0, a cell index out of
- * range, semi-axes <= 0, density <= 0, or a body not inside the fluid region
- * of a non-periodic axis. */
+ * range, semi-axes <= 0, density <= 0, an unknown shape, a spherocylinder
+ * whose semi_axes are not (L/2, r, r) with L/2 >= r, a body not inside the
+ * fluid region of a non-periodic axis, or a body on the fluid layer next to a
+ * free-slip wall. */
 lbm_status lbm_set_particles(lbm_ctx *ctx, const lbm_particle *p, int n);
 
 /* Advance nsteps time steps, asynchronously on the context's stream.  One step
@@ -167,22 +169,29 @@ lbm_status lbm_set_particles(lbm_ctx *ctx, const lbm_particle *p, int n);
  * force/torque sums (Eqs. LBMCollide, LBMStream, LBMMovWall,
  * LBMhydrodynForce); the rigid-body update; the re-mapping of obstacle cells
  * with equilibrium refill of uncovered cells (Sec. 4.2).
- * Errors: LBM_ERR_ARG for nsteps < 0; LBM_ERR_STATE after an earlier
- * numeric error; LBM_ERR_CUDA. */
+ * Device-side conditions (a non-finite force or body state, a body reaching
+ * the fluid layer next to a free-slip wall, a bounded wait that ran out) are
+ * reported by the next synchronising call (lbm_sync, lbm_get_forces).
+ * Errors: LBM_ERR_ARG for nsteps < 0; LBM_ERR_STATE after such a condition
+ * was reported; LBM_ERR_CUDA. */
 lbm_status lbm_step(lbm_ctx *ctx, int nsteps);
 
-/* Wait for all queued work; reports LBM_ERR_NUMERIC if a non-finite force was
- * met since the last check. */
+/* Wait for all queued work; reports LBM_ERR_NUMERIC (non-finite force or body
+ * state), LBM_ERR_UNSUPPORTED (a body reached the fluid layer next to a
+ * free-slip wall) or LBM_ERR_TIMEOUT (a bounded device wait ran out) if met
+ * since the last check; the context then refuses further steps. */
 lbm_status lbm_sync(lbm_ctx *ctx);
 
 /* Hydrodynamic force and torque (Eq. LBMhydrodynForce; torque about the
  * centre of mass with lever arm x_s - x_C) of the last completed step, for the
  * first n particles, as force3n[3*i + a], torque3n[3*i + a].  External loads
- * are not included.  Synchronises.  Either pointer may be NULL. */
+ * are not included.  Synchronises and reports the device-side conditions as
+ * lbm_sync does.  Either pointer may be NULL. */
 lbm_status lbm_get_forces(lbm_ctx *ctx, double *force3n, double *torque3n, int n);
 
 /* Momentum handed per step to the y = 0 and y = ny-1 wall layers of lattice
- * `cell` in the last step: f6[0..2] low wall, f6[3..5] high wall. */
+ * `cell` in the last step: f6[0..2] low wall, f6[3..5] high wall (no-slip
+ * walls; free-slip walls book no momentum). */
 lbm_status lbm_get_wall_forces(lbm_ctx *ctx, int cell, double *f6);
 
 /* Current particle states (pose, velocities) of the first n particles. */
@@ -190,8 +199,9 @@ lbm_status lbm_get_particles(lbm_ctx *ctx, lbm_particle *p, int n);
 
 /* Set external force/torque of the first n particles (host arrays of 3n
  * doubles; either may be NULL to leave that part unchanged).  Asynchronous
- * host-to-device copy on the context's stream; the arrays may be reused
- * as soon as the call returns. */
+ * host-to-device copy on the context's stream: pageable arrays may be reused
+ * as soon as the call returns, page-locked ones must stay unchanged until the
+ * next synchronising call. */
 lbm_status lbm_set_external(lbm_ctx *ctx, const double *force3n, const double *torque3n, int n);
 
 /* Fields of lattice `cell` in canonical form (see Conventions): density
