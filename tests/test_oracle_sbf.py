@@ -1,0 +1,137 @@
+"""Pins of the slender-body oracle (Sec. 3, `oracle/sbf.py`).
+
+* The non-local operator Kbar is diagonal on Legendre polynomials with
+  eigenvalues -2 sum_{i<=n} 1/i: checked by direct quadrature of Eq. Kbar.
+* A single fibre's translational mobility equals Cox's slender-spheroid
+  friction coefficients (independent derivation, `oracle/closed_forms.py`),
+  which pins the geometry parameter d and the local operator.
+* Two fibres far apart: the velocity one induces on the other tends to the
+  Stokeslet of its force, S(R) F / (8 pi mu).
+* Two identical parallel fibres side by side falling broadside move with
+  equal velocities, faster than one alone, without turning.
+* Reciprocity: the velocity fibre 1 gets from a force on fibre 2 equals, as a
+  matrix, the transpose of the velocity fibre 2 gets from a force on fibre 1.
+* The Legendre and quadrature truncations converge.
+* Heun's method: a torque-driven fibre turns at the closed-form rate with
+  second-order error in the time step.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import closed_forms as cf
+from oracle import sbf
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 7])
+def test_kbar_is_diagonal_on_legendre(n):
+    integrate = pytest.importorskip("scipy.integrate")
+    c = np.zeros(n + 1)
+    c[n] = 1.0
+    P = lambda x: np.polynomial.legendre.legval(x, c)  # noqa: E731
+    for s in (-0.83, -0.2, 0.37, 0.91):
+        val = integrate.quad(lambda t: (P(t) - P(s)) / abs(t - s), -1.0, 1.0, points=[s], limit=200,
+                             epsabs=1e-13, epsrel=1e-12)[0]
+        assert val == pytest.approx(sbf.kbar_eigenvalue(n) * P(s), abs=1e-9)
+
+
+@pytest.mark.parametrize("aspect", [8.0, 20.0, 50.0])
+def test_single_fibre_translation_matches_cox_spheroid(aspect):
+    L, mu = 2.0, 1.3
+    r = L / aspect
+    f = sbf.Fibres([(0, 0, 0)], [(0.3, -0.5, 0.81)], L / 2, r, mu)
+    p = f.p[0]
+    Fpar, Fperp = 2.0 * p, np.cross(p, (0, 0, 1.0))
+    Fperp *= 1.7 / np.linalg.norm(Fperp)
+    g_par, g_perp = cf.cox_coefficients(mu, L, r, shape="spheroid")
+    _, v, w = f.solve([Fpar], [(0, 0, 0)])
+    assert np.allclose(v[0], Fpar / g_par, rtol=1e-13, atol=0)
+    assert np.allclose(w[0], 0.0, atol=1e-15)
+    _, v, _ = f.solve([Fperp], [(0, 0, 0)])
+    assert np.allclose(v[0], Fperp / g_perp, rtol=1e-13, atol=1e-17)
+
+
+def test_far_fibre_sees_the_stokeslet():
+    mu = 1.0
+    R = np.array([0.0, 300.0, 40.0])
+    f = sbf.Fibres([(0, 0, 0), R], [(1, 0, 0), (0.2, 0.7, 0.3)], 1.0, 0.1, mu)
+    F2 = np.array([0.3, -1.0, 0.5])
+    _, v, _ = f.solve([(0, 0, 0), F2], [(0, 0, 0), (0, 0, 0)])
+    Rv = -R  # from fibre 2 to fibre 1
+    d = np.linalg.norm(Rv)
+    S = (np.eye(3) + np.outer(Rv, Rv) / d ** 2) / d
+    expected = S @ F2 / (8 * math.pi * mu)
+    assert np.allclose(v[0], expected, rtol=1e-3, atol=1e-4 * np.abs(expected).max())
+
+
+def test_side_by_side_fibres_fall_together():
+    mu, L = 1.0, 2.0
+    f2 = sbf.Fibres([(0, -0.6, 0), (0, 0.6, 0)], [(1, 0, 0), (1, 0, 0)], L / 2, 0.08, mu)
+    f1 = sbf.Fibres([(0, 0, 0)], [(1, 0, 0)], L / 2, 0.08, mu)
+    F = np.array([0.0, 0.0, -1.0])
+    _, v2, w2 = f2.solve([F, F], [(0, 0, 0), (0, 0, 0)])
+    _, v1, _ = f1.solve([F], [(0, 0, 0)])
+    assert np.allclose(v2[0], v2[1], rtol=1e-12, atol=1e-15)
+    assert np.allclose(w2, 0.0, atol=1e-12)
+    assert v2[0][2] < v1[0][2] < 0  # the pair settles faster
+
+
+def test_reciprocity_of_the_pair_mobility():
+    mu = 0.9
+    f = sbf.Fibres([(0, 0, 0), (0.7, 2.3, -0.4)], [(1, 0.2, 0), (0.1, 0.4, 1.0)], 1.0, 0.07, mu, n_modes=6,
+                   n_quad=40)
+    M12 = np.zeros((3, 3))
+    M21 = np.zeros((3, 3))
+    for a in range(3):
+        e = np.zeros(3)
+        e[a] = 1.0
+        _, v, _ = f.solve([(0, 0, 0), e], [(0, 0, 0), (0, 0, 0)])
+        M12[:, a] = v[0]
+        _, v, _ = f.solve([e, (0, 0, 0)], [(0, 0, 0), (0, 0, 0)])
+        M21[:, a] = v[1]
+    assert np.allclose(M12, M21.T, rtol=1e-12, atol=1e-13 * np.abs(M12).max())
+
+
+def test_truncations_converge():
+    args = ([(0, 0, 0), (0.5, 1.4, 0.2)], [(1, 0, 0.3), (0.3, 1.0, 0.0)], 1.0, 0.06, 1.0)
+    F = [(0, 0, -1.0), (0.2, 0, -1.0)]
+    Mt = [(0, 0.1, 0), (0, 0, 0)]
+    ref = sbf.Fibres(*args, n_modes=8, n_quad=64).solve(F, Mt)
+    for nm, nq in ((5, 24), (6, 32)):
+        got = sbf.Fibres(*args, n_modes=nm, n_quad=nq).solve(F, Mt)
+        for a, b in zip(got[1:], ref[1:]):
+            assert np.allclose(a, b, rtol=2e-3, atol=2e-4 * np.abs(b).max())
+
+
+def test_heun_rotation_is_second_order():
+    mu, L, r = 1.0, 2.0, 0.1
+    Mz = 0.05
+    d = sbf.geometry_parameter(r / L)
+    omega = 3 * d * Mz / (2 * math.pi * mu * L ** 3)
+    T = 1.0 / omega  # one radian
+    errs = []
+    for nsteps in (20, 40):
+        f = sbf.Fibres([(0, 0, 0)], [(1, 0, 0)], L / 2, r, mu)
+        for _ in range(nsteps):
+            f.step([(0, 0, 0)], [(0, 0, Mz)], T / nsteps)
+        angle = math.atan2(f.p[0][1], f.p[0][0])
+        errs.append(abs(angle - omega * T))
+    assert errs[1] < errs[0] / 3.0
+
+
+def test_rotation_rate_against_tirado_as_the_paper_reports():
+    """Sec. 5.2: the SBF angular velocities exceed Tirado's (cylinder of the
+    full length) by almost 90 % at 1/eps = 4 and by more than 50 % at 14."""
+    mu, r = 1e-3, 4e-5
+    ratios = {}
+    for aspect in (4, 14):
+        L = aspect * r
+        f = sbf.Fibres([(0, 0, 0)], [(1, 0, 0)], L / 2, r, mu)
+        M = np.array([0.0, 0.0, 1e-15])
+        _, _, w = f.solve([(0, 0, 0)], [M])
+        omega_sbf = np.linalg.norm(w[0])
+        omega_tir = M[2] / cf.tirado_coefficients(mu, L, r)[2]
+        ratios[aspect] = omega_sbf / omega_tir
+    assert 1.80 < ratios[4] < 1.90
+    assert 1.50 < ratios[14] < 1.60
