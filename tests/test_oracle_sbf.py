@@ -135,3 +135,61 @@ def test_rotation_rate_against_tirado_as_the_paper_reports():
         ratios[aspect] = omega_sbf / omega_tir
     assert 1.80 < ratios[4] < 1.90
     assert 1.50 < ratios[14] < 1.60
+
+
+# --------------------------------------------------------------------------
+# periodic box (the form the paper's tumbling runs use)
+# --------------------------------------------------------------------------
+
+def _direct(Lb, xi):
+    b = sbf.PeriodicStokeslet.__new__(sbf.PeriodicStokeslet)
+    b.Lb, b.xi, b.n_real, b.n_fourier = Lb, xi, 3, 12
+    return b
+
+
+def test_ewald_split_does_not_depend_on_the_splitting_parameter():
+    pytest.importorskip("scipy.special")
+    R = np.array([[0.13, 0.31, -0.22], [0.0, 0.0, 0.0], [0.4, -0.45, 0.1], [0.02, 0.0, 0.01]])
+    ref = _direct(1.0, 3.5).correction_direct(R)
+    for xi in (5.0, 7.0):
+        assert np.allclose(_direct(1.0, xi).correction_direct(R), ref, rtol=1e-10, atol=1e-11)
+
+
+def test_periodic_correction_at_the_origin_is_hasimotos():
+    """A force in a periodic cubic array moves its point by C(0) F / (8 pi mu)
+    relative to free space; Hasimoto's sphere-array drag, F = 6 pi mu a U K with
+    K = 1 + 1.7601 c^(1/3) + ..., c = 4/3 pi a^3 / Lb^3, gives
+    C(0) = -(8/6) 1.7601 (4 pi / 3)^(1/3) / Lb."""
+    pytest.importorskip("scipy.special")
+    Lb = 2.5
+    C0 = _direct(Lb, 3.0).correction_direct(np.zeros((1, 3)))[0]
+    expected = -(8.0 / 6.0) * 1.7601 * (4 * math.pi / 3) ** (1 / 3) / Lb
+    assert np.allclose(C0, expected * np.eye(3), rtol=2e-5, atol=1e-9)
+
+
+def test_reflection_rule_and_interpolation():
+    pytest.importorskip("scipy.special")
+    box = sbf.PeriodicStokeslet(1.0, n_grid=12)
+    rng = np.random.default_rng(3)
+    R = rng.uniform(-0.5, 0.5, size=(6, 3))
+    direct = box.correction_direct(R)
+    for s in ([1, -1, 1], [-1, -1, 1], [-1, 1, -1]):
+        s = np.array(s, dtype=float)
+        refl = box.correction_direct(R * s)
+        assert np.allclose(refl, direct * np.outer(s, s)[None], rtol=1e-10, atol=1e-11)
+    interp = box.correction(R)
+    assert np.abs(interp - direct).max() < 2e-3 * 3.78
+
+
+def test_single_fibre_in_a_periodic_box_feels_its_images():
+    pytest.importorskip("scipy.special")
+    Lb, mu = 40.0, 1.0
+    box = sbf.PeriodicStokeslet(Lb, n_grid=12)
+    F = np.array([0.0, 0.0, -1.0])
+    free = sbf.Fibres([(0, 0, 0)], [(1, 0, 0)], 1.0, 0.1, mu)
+    per = sbf.Fibres([(0, 0, 0)], [(1, 0, 0)], 1.0, 0.1, mu, box=box)
+    _, vf, _ = free.solve([F], [(0, 0, 0)])
+    _, vp, wp = per.solve([F], [(0, 0, 0)])
+    C0 = box.correction_direct(np.zeros((1, 3)))[0]
+    assert np.allclose(vp[0] - vf[0], C0 @ F / (8 * math.pi * mu), rtol=1e-2)
+    assert np.allclose(wp, 0.0, atol=1e-12)
