@@ -193,3 +193,53 @@ def test_single_fibre_in_a_periodic_box_feels_its_images():
     C0 = box.correction_direct(np.zeros((1, 3)))[0]
     assert np.allclose(vp[0] - vf[0], C0 @ F / (8 * math.pi * mu), rtol=1e-2)
     assert np.allclose(wp, 0.0, atol=1e-12)
+
+
+def _tumbling_pair(aspect, dist_dx, box_dx, dx, r_dx, mu, Fz, dt=0.01, t_end=9.0):
+    """Two fibres aligned with gravity (z), dist apart in x, in a periodic cube:
+    the period (successive times the pair is aligned with gravity again), the
+    sedimentation distance per period and the velocity extremes of one fibre."""
+    r = r_dx * dx
+    L = aspect * r
+    box = sbf.PeriodicStokeslet(box_dx * dx, n_grid=24)
+    d = dist_dx * dx
+    f = sbf.Fibres([(-d / 2, 0, 0), (d / 2, 0, 0)], [(0, 0, 1), (0, 0, 1)], L / 2, r, mu, n_modes=5, n_quad=24,
+                   box=box)
+    F = [(0, 0, Fz), (0, 0, Fz)]
+    Mt = [(0, 0, 0), (0, 0, 0)]
+    t, z, ang, vel = [], [], [], []
+    for n in range(int(t_end / dt)):
+        _, v, _ = f.solve(F, Mt)
+        t.append(n * dt)
+        z.append(f.x[0][2])
+        ang.append(math.atan2(f.p[0][0], f.p[0][2]))
+        vel.append(v[0].copy())
+        f.step(F, Mt, dt)
+    ang = np.unwrap(np.array(ang))
+    k = np.floor(ang / math.pi)
+    cross = np.nonzero(np.diff(k) != 0)[0]
+    a, b = cross[0], cross[1]
+    T = t[b] - t[a]
+    D = z[b] - z[a]
+    V = np.array(vel[a:b])
+    return T, D, V
+
+
+@pytest.mark.parametrize("row", [0, 1])
+def test_tumbling_pair_reproduces_the_papers_slender_body_table(row):
+    """Sec. 6.4: the slender-body rows of the tumbling-pair table (periodic
+    cube of 576 dx, water, r = 4 dx, 1/eps = 12)."""
+    pytest.importorskip("scipy.special")
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "table_sbf_tumbling.json")))
+    g = gold["rows"][row]
+    Fz = gold["force_z_N"][str(g["inverse_eps"])]
+    T, D, V = _tumbling_pair(g["inverse_eps"], g["dist_dx"], g["box_dx"], gold["dx_m"], gold["radius_dx"],
+                             gold["mu"], Fz)
+    assert abs(V[:, 0]).max() * 1e6 == pytest.approx(g["ux_max_um_s"], rel=0.01)
+    assert V[:, 2].min() * 1e3 == pytest.approx(g["uz_min_mm_s"], rel=0.015)
+    assert V[:, 2].max() * 1e3 == pytest.approx(g["uz_max_mm_s"], rel=0.015)
+    assert D / T * 1e3 == pytest.approx(g["U_mm_s"], rel=0.02)
+    assert T == pytest.approx(g["T_s"], rel=0.03)
+    assert D * 1e3 == pytest.approx(g["D_mm"], rel=0.04)
