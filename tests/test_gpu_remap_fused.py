@@ -4,8 +4,8 @@ barriers) against the separate kernels.  The passes do the same arithmetic,
 but the sweep's FP64 force sums come from atomics in no fixed order, so two
 runs of either form agree to rounding only: flags and particle-id maps must be
 identical, body states and fields equal to a few units of rounding of the
-storage form.  The parity tests against the FP64 oracle run the fused form
-(the default).
+storage form.  The parity tests against the FP64 oracle run the separate
+kernels (the default); these tests switch the fused form on explicitly.
 """
 import numpy as np
 import pytest
