@@ -94,6 +94,10 @@ SIGNATURES = {
     "lbm_mlp_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_float, C.c_void_p]),
     "lbm_mlp_get_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "lbm_mlp_destroy": (C.c_int, [C.c_void_p]),
+    "lbm_sbf_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "lbm_sbf_set_fibres": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "lbm_sbf_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "lbm_sbf_destroy": (C.c_int, [C.c_void_p]),
     "lbm_destroy": (C.c_int, [C.c_void_p]),
     "lbm_last_error": (C.c_char_p, [C.c_void_p]),
     "lbm_status_string": (C.c_char_p, [C.c_int]),
@@ -323,6 +327,49 @@ def lbm_mlp_get_params(m):
 
 def lbm_mlp_destroy(m):
     _check(load().lbm_mlp_destroy(m))
+
+
+# --- slender-body formulation (include/lbm_sbf.h) --------------------------
+
+class SlenderBodies:
+    """Rigid straight fibres in unbounded Stokes flow (slender-body
+    formulation) on the GPU: velocities for given forces and torques."""
+
+    def __init__(self, centres, tangents, half_lengths, radii, mu: float, n_modes: int = 5, n_quad: int = 24,
+                 stream=None):
+        x = np.ascontiguousarray(centres, dtype=np.float64).reshape(-1, 3)
+        self.M = len(x)
+        h = C.c_void_p()
+        _check(load().lbm_sbf_create(self.M, n_modes, n_quad, float(mu), stream, C.byref(h)))
+        self.h = h
+        self.set_fibres(x, tangents, half_lengths, radii)
+
+    def set_fibres(self, centres, tangents, half_lengths, radii):
+        M = self.M
+        self._geo = [np.ascontiguousarray(centres, dtype=np.float64).reshape(M, 3),
+                     np.ascontiguousarray(tangents, dtype=np.float64).reshape(M, 3),
+                     np.ascontiguousarray(np.broadcast_to(half_lengths, (M,)), dtype=np.float64),
+                     np.ascontiguousarray(np.broadcast_to(radii, (M,)), dtype=np.float64)]
+        _check(load().lbm_sbf_set_fibres(self.h, *[_ptr(a) for a in self._geo]))
+
+    def solve(self, forces, torques):
+        F = np.ascontiguousarray(forces, dtype=np.float64).reshape(self.M, 3)
+        T = np.ascontiguousarray(torques, dtype=np.float64).reshape(self.M, 3)
+        xdot = np.zeros((self.M, 3))
+        pdot = np.zeros((self.M, 3))
+        _check(load().lbm_sbf_solve(self.h, _ptr(F), _ptr(T), _ptr(xdot), _ptr(pdot)))
+        return xdot, pdot
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().lbm_sbf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---------------------------------------------------------------------------
