@@ -86,3 +86,28 @@ def test_null_context_is_rejected(lib):
     assert lib.lbm_step(None, 1) == lbm.LBM_ERR_ARG
     assert lib.lbm_destroy(None) == lbm.LBM_ERR_ARG
     assert lib.lbm_last_error(None) == b"null context"
+
+
+def test_free_slip_descriptor_rules_without_gpu(lib):
+    """A free-slip axis cannot be periodic, and free-slip y walls cannot move
+    (the moving walls of Sec. 4 are no-slip); both are refused on the host."""
+    from paper_1503_06869_gb300 import lbm
+    from lbm_inputs import shear_lattice
+    h = C.c_void_p()
+    d = lbm.grid_desc(shear_lattice(8, 8, 8, 0.8, 0.01))
+    d.free_slip[0] = 1                      # x is periodic in the shear lattice
+    assert lib.lbm_create(C.byref(d), C.byref(h)) == lbm.LBM_ERR_ARG and not h.value
+    d = lbm.grid_desc(shear_lattice(8, 8, 8, 0.8, 0.01))
+    d.free_slip[1] = 1                      # y walls move at -/+ uw
+    assert lib.lbm_create(C.byref(d), C.byref(h)) == lbm.LBM_ERR_ARG and not h.value
+
+
+@pytest.mark.parametrize("M,N,nq,mu", [(0, 5, 24, 1.0), (65, 5, 24, 1.0), (2, 1, 24, 1.0), (2, 11, 24, 1.0),
+                                       (2, 5, 1, 1.0), (2, 5, 65, 1.0), (2, 5, 24, 0.0), (2, 5, 24, float("nan"))])
+def test_slender_body_sizes_are_checked_before_touching_the_gpu(lib, M, N, nq, mu):
+    from paper_1503_06869_gb300 import lbm
+    h = C.c_void_p()
+    assert lib.lbm_sbf_create(M, N, nq, mu, None, C.byref(h)) == lbm.LBM_ERR_ARG
+    assert not h.value
+    assert lib.lbm_sbf_create(2, 5, 24, 1.0, None, None) == lbm.LBM_ERR_ARG
+    assert lib.lbm_sbf_destroy(None) == lbm.LBM_ERR_ARG
