@@ -111,3 +111,39 @@ def test_slender_body_sizes_are_checked_before_touching_the_gpu(lib, M, N, nq, m
     assert not h.value
     assert lib.lbm_sbf_create(2, 5, 24, 1.0, None, None) == lbm.LBM_ERR_ARG
     assert lib.lbm_sbf_destroy(None) == lbm.LBM_ERR_ARG
+
+
+def test_a_c_program_links_and_calls_the_library(lib, tmp_path):
+    """The headers compile as C99 with warnings as errors and a C program
+    links against the shared library and gets its host-side answers (no
+    call that needs a device)."""
+    from paper_1503_06869_gb300 import lbm
+    prog = tmp_path / "use.c"
+    prog.write_text(r'''
+#include <stdio.h>
+#include <string.h>
+#include "lbm.h"
+#include "lbm_sbf.h"
+int main(void) {
+    lbm_ctx *c = NULL;
+    lbm_sbf *s = NULL;
+    lbm_grid_desc d;
+    memset(&d, 0, sizeof d);
+    d.nx = 2; d.ny = 8; d.nz = 8; d.tau = 0.8; d.magic = 3.0 / 16.0; d.rho0 = 1.0;
+    if (lbm_create(&d, &c) != LBM_ERR_ARG || c) return 1;
+    if (lbm_create(NULL, &c) != LBM_ERR_ARG) return 2;
+    if (lbm_sbf_create(0, 5, 24, 1.0, NULL, &s) != LBM_ERR_ARG || s) return 3;
+    if (lbm_destroy(NULL) != LBM_ERR_ARG || lbm_sbf_destroy(NULL) != LBM_ERR_ARG) return 4;
+    if (strcmp(lbm_status_string(LBM_ERR_ARG), "invalid argument") != 0) return 5;
+    if (strcmp(lbm_last_error(NULL), "null context") != 0) return 6;
+    puts("ok");
+    return 0;
+}
+''')
+    exe = tmp_path / "use"
+    libdir = os.path.dirname(lbm.LIB_PATH)
+    name = os.path.basename(lbm.LIB_PATH)[3:-3]
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    str(prog), "-o", str(exe), "-L", libdir, f"-l{name}", f"-Wl,-rpath,{libdir}"], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout, r.stderr)
