@@ -157,6 +157,38 @@ def test_uniform_flow_is_a_fixed_point():
     assert np.allclose(rho, 1.0, atol=1e-14, rtol=0)
 
 
+@pytest.mark.parametrize("shape", [0, 1])
+def test_body_translating_with_a_uniform_flow_is_a_fixed_point(shape):
+    """Moving-obstacle bounce-back (Eq. LBMMovWall) returns f~_q - 6 w_q rho0
+    c_q . u_s, and the equilibrium's odd part is exactly f^eq_qbar - f^eq_q =
+    -6 w_q rho0 c_q . u: a body translating at U inside fluid at rest in the
+    frame of U (uniform f^eq(rho0, U)) leaves every population unchanged.  The
+    force vanishes too: the links in directions q and qbar of a closed body
+    in a periodic box are equally many and carry equal even parts.  A wrong
+    sign, factor or direction in the bounce-back breaks both."""
+    lat = Lattice(16, 14, 12, tau=0.75, periodic=(1, 1, 1))
+    U = np.array([0.03, -0.02, 0.01])
+    t = np.array([0.6, 0.5, -0.3])
+    body = Particle(pos=(7.3, 6.6, 5.9), quat=quat_from_axis(t / np.linalg.norm(t)), semi_axes=(4.5, 2.2, 2.2),
+                    vel=tuple(U), fixed=1, shape=shape)
+    s = oracle.Sim(lat, [body])
+    _fill_equilibrium(s, 1.0, U)
+    s.step(12)
+    rho, u, fl, pid, pdf = s.fields()
+    m = fl == 0
+    assert (~m).sum() > 50
+    feq = oracle.equilibrium(1.0, U, 1.0)
+    assert np.abs(pdf[:, m] - feq[:, None]).max() < 1e-15
+    F, M = s.forces()
+    assert np.abs(F).max() < 1e-13 and np.abs(M).max() < 1e-12
+    # the same body at rest in that flow is not a fixed point and feels drag along U
+    s2 = oracle.Sim(lat, [Particle(pos=body.pos, quat=body.quat, semi_axes=body.semi_axes, fixed=1, shape=shape)])
+    _fill_equilibrium(s2, 1.0, U)
+    s2.step(1)
+    F2, _ = s2.forces()
+    assert F2[0] @ U > 1e-3 * np.linalg.norm(U)
+
+
 def test_mass_conserved_with_moving_walls():
     lat = shear_lattice(12, 16, 10, 0.8, 0.03)
     s = oracle.Sim(lat)
