@@ -311,7 +311,10 @@ lbm_status lbm_set_momentum_stabilisation(lbm_ctx *ctx, int enable);
 lbm_status lbm_autotune(lbm_ctx *ctx, int *block, int *grid);
 
 /* CUDA graphs: when enabled, lbm_step replays a captured two-step graph for
- * pairs of steps (default on). */
+ * pairs of steps that start on an even step, and a captured one-step graph
+ * (one per parity) for a leading odd step or a trailing single step (default
+ * on; needs a non-NULL stream).  Replay and eager launches give the same
+ * state. */
 lbm_status lbm_set_graphs(lbm_ctx *ctx, int enable);
 
 /* Sweep-kernel timing: when enabled, every sweep launch is bracketed by CUDA
