@@ -314,7 +314,8 @@ lbm_status lbm_autotune(lbm_ctx *ctx, int *block, int *grid);
  * pairs of steps that start on an even step, and a captured one-step graph
  * (one per parity) for a leading odd step or a trailing single step (default
  * on; needs a non-NULL stream).  Replay and eager launches give the same
- * state. */
+ * flags and particle ids, and fields equal up to the order of the FP64
+ * force sums. */
 lbm_status lbm_set_graphs(lbm_ctx *ctx, int enable);
 
 /* Sweep-kernel timing: when enabled, every sweep launch is bracketed by CUDA
