@@ -163,3 +163,24 @@ def test_the_readme_c_example_compiles_and_links(lib, tmp_path):
     subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
                     str(prog), "-o", str(tmp_path / "readme"), "-L", libdir, f"-l{name}",
                     f"-Wl,-rpath,{libdir}"], check=True)
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """No CPU fallback: without the built library the binding raises."""
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_1503_06869_gb300 import lbm\n"
+            "try:\n    lbm.load(%r)\nexcept ImportError as e:\n    print('raised', e)\n") % (
+        ROOT, str(tmp_path / "liblbm_missing.so"))
+    r = subprocess.run([os.sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.startswith("raised CUDA library not built"), (r.stdout, r.stderr)
+
+
+def test_the_package_never_reaches_the_oracle():
+    """The product package imports nothing from oracle/ (test infrastructure)."""
+    pkg = os.path.join(ROOT, "paper_1503_06869_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(from|import)\s+oracle\b", src, flags=re.M), f
+                assert "lbm_oracle" not in src, f
