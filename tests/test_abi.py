@@ -184,3 +184,15 @@ def test_the_package_never_reaches_the_oracle():
                 src = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(from|import)\s+oracle\b", src, flags=re.M), f
                 assert "lbm_oracle" not in src, f
+
+
+def test_the_oracle_never_reaches_the_package():
+    """The oracle shares no code with the CUDA library: it neither imports the
+    package nor includes its headers or sources."""
+    odir = os.path.join(ROOT, "oracle")
+    for f in os.listdir(odir):
+        if f.endswith((".py", ".c", ".h")):
+            src = open(os.path.join(odir, f)).read()
+            assert not re.search(r"^\s*(from|import)\s+paper_1503_06869_gb300\b", src, flags=re.M), f
+            assert not re.search(r'#include\s+"(lbm\.h|lbm_sbf\.h|lbm_internal\.cuh)"', src), f
+            assert "csrc" not in src, f
