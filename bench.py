@@ -82,16 +82,17 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle-reason samples during the timed region."""
+    """nvidia-smi clock / throttle-reason samples (every 100 ms, time-stamped)
+    kept only inside the windows marked with mark_start / mark_stop."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu: int):
         self.gpu = gpu
         self.proc = None
-        self.lines = []
+        self.windows = []
 
     def start(self):
         try:
@@ -101,35 +102,50 @@ class ClockSampler:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
+        time.sleep(0.3)  # the first sample precedes the timed region
+
+    def mark_start(self):
+        self.windows.append([time.time(), None])
+
+    def mark_stop(self):
+        if self.windows:
+            self.windows[-1][1] = time.time()
 
     def stop(self):
         if self.proc is None:
             return None
-        time.sleep(0.25)
+        time.sleep(0.15)
         self.proc.terminate()
         try:
             out, _ = self.proc.communicate(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
             out, _ = self.proc.communicate()
-        sm, mx, reasons = [], None, set()
+        import datetime
+        sm, mx, reasons, total = [], None, set(), 0
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in out.strip().splitlines():
             parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
+            total += 1
             try:
-                sm.append(float(parts[1]))
-                mx = float(parts[2])
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                sm_v = float(parts[2])
+                mx = float(parts[3])
             except ValueError:
                 continue
-            for n, v in zip(names, parts[5:9]):
+            if not any(w0 <= ts <= (w1 or ts) for w0, w1 in self.windows):
+                continue
+            sm.append(sm_v)
+            for n, v in zip(names, parts[6:10]):
                 if v.lower() == "active":
                     reasons.add(n)
         if not sm:
-            return None
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": total,
+                    "samples_in_timed_region": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": total, "samples_in_timed_region": len(sm)}
 
 
 def dist_setup(n_gpus: int):
@@ -271,23 +287,219 @@ def run_sequential(args, w, rank, world):
     return 0
 
 
+PREC_NAMES = {"f64": "f64", "f32": "f32", "f16": "f16", "bf16": "bf16"}
+
+
+def fluid_cells(lbm, h, lattices):
+    n = 0
+    for c, lat in enumerate(lattices):
+        f = lbm.lbm_get_fields(h, lat.ncells, c, rho=False, u=False, flags=True, pid=False)
+        n += int((f["flags"] == 0).sum())
+    return n
+
+
+def timed_steps(sim, lbm, steps, world, clocks, min_region_s, max_reps=400):
+    """Repeat the timed region -- exactly `steps` steps (CUDA-graph replay),
+    bracketed by a barrier and a device synchronisation on both sides, CUDA
+    events on the context's stream -- until the repetitions cover about
+    min_region_s; returns the per-repetition times (ms, max over ranks) and
+    the kernels launched per repetition."""
+    import torch
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    times, launches = [], 0
+    total = 0.0
+    while True:
+        l0 = lbm.lbm_get_launch_count(sim.h)
+        barrier(world)
+        torch.cuda.synchronize()
+        if clocks is not None:
+            clocks.mark_start()
+        ev0.record(sim.stream)
+        sim.step(steps)
+        ev1.record(sim.stream)
+        torch.cuda.synchronize()
+        if clocks is not None:
+            clocks.mark_stop()
+        barrier(world)
+        launches = lbm.lbm_get_launch_count(sim.h) - l0
+        ms = max_over_ranks(ev0.elapsed_time(ev1), world)
+        times.append(ms)
+        total += ms
+        # every rank takes the same decision (the times are the max over ranks)
+        if total >= 1e3 * min_region_s or len(times) >= max_reps:
+            break
+    return times, launches
+
+
+def measure(args, w, prec, world, local, launch=None, cpt=None, closure_params=None, clocks=None,
+            min_region_s=1.0, steps=None, e2e_steps=0):
+    """One workload in one storage form: autotuned launch, warm-up, the timed
+    repetitions, the sweep kernel timed alone (eager launches with CUDA events
+    around every sweep), optionally the end-to-end loop through the C
+    interface with host buffers.  Returns a dict of results."""
+    import torch
+    from paper_1503_06869_gb300 import lbm
+    steps = steps or args.steps
+    sim = lbm.Simulation(w.lattices, w.particles, prec=prec, device=local)
+    h = sim.h
+    if closure_params is not None:
+        lbm.lbm_set_closure(h, closure_params)
+    if args.remap_fused:
+        lbm.lbm_set_remap_fused(h, True)
+    if launch is None:
+        lbm.lbm_autotune(h)
+    else:
+        lbm.lbm_set_launch(h, launch, 0)
+        if cpt:
+            lbm.lbm_set_cells_per_thread(h, cpt)
+    info = lbm.lbm_get_info(h)
+    sim.step(args.warmup)
+    sim.sync()
+    nfluid = fluid_cells(lbm, h, w.lattices)
+    times, launches = timed_steps(sim, lbm, steps, world, clocks, min_region_s)
+    ms_rep = statistics.median(times)
+    ms_step = ms_rep / steps
+
+    # the sweep kernel alone: the same number of steps again, every sweep
+    # launch bracketed by CUDA events on the context's stream (eager launches:
+    # a graph replay has no events between its kernels)
+    lbm.lbm_set_sweep_timing(h, True)
+    sim.step(steps)
+    sweep_ms, sweep_n = lbm.lbm_get_sweep_timing(h)
+    lbm.lbm_set_sweep_timing(h, False)
+    sim.sync()
+
+    peak, peak_kind = measured_peaks()
+    bpp = BYTES_PER_POP[prec]
+    bytes_per_launch = 38 * bpp * nfluid
+    sweep_avg_ms = sweep_ms / max(sweep_n, 1)
+    achieved = bytes_per_launch / (sweep_avg_ms * 1e-3) / 1e9
+    step_achieved = bytes_per_launch / (ms_step * 1e-3) / 1e9
+    res = {"workload": w.name, "prec": prec, "cells": int(w.ncells), "fluid_cells": int(nfluid),
+           "particles": len(w.particles), "ms_per_step": ms_step, "reps": len(times), "steps_per_rep": steps,
+           "rep_ms_min": min(times), "rep_ms_max": max(times), "launches_per_rep": int(launches),
+           "mlups": w.ncells * steps * world / (ms_rep * 1e-3) / 1e6,
+           "fluid_mlups": nfluid * steps * world / (ms_rep * 1e-3) / 1e6,
+           "particle_steps_per_s": len(w.particles) * steps * world / (ms_rep * 1e-3),
+           "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                        "frac": round(achieved / peak, 4), "traffic": sweep_traffic(w.name, prec),
+                        "kernel": "sweep", "bytes_per_launch": bytes_per_launch,
+                        "avg_launch_ms": round(sweep_avg_ms, 5),
+                        "avg_launch_source": "eager pass of the same step count, CUDA events around every "
+                                             "sweep launch on the context's stream",
+                        "step_achieved": round(step_achieved, 1), "step_frac": round(step_achieved / peak, 4),
+                        "peak_kind": f"{peak_kind} hbm_gbs"},
+           "launch": {"block": info.sweep_block, "grid": info.sweep_grid, "cells_per_thread": info.cells_per_thread,
+                      "split": bool(info.sweep_split), "remap_fused": bool(info.remap_fused)}}
+    if e2e_steps:
+        # every step: H2D of the particles' external loads from pinned memory,
+        # the step, D2H of the hydrodynamic force/torque (synchronising)
+        npart = max(len(w.particles), 1)
+        ext = torch.zeros((npart, 3), dtype=torch.float64).pin_memory()
+        Fh = torch.zeros((npart, 3), dtype=torch.float64).pin_memory()
+        Mh = torch.zeros((npart, 3), dtype=torch.float64).pin_memory()
+        extn, Fn, Mn = ext.numpy(), Fh.numpy(), Mh.numpy()
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            lbm.lbm_set_external(h, extn, None, len(w.particles))
+            lbm.lbm_step(h, 1)
+            lbm.lbm_get_forces(h, len(w.particles), Fn, Mn)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        e2e_s = max_over_ranks(t1 - t0, world)
+        res["e2e"] = {"value": round(w.ncells * e2e_steps * world / e2e_s / 1e6, 1), "unit": "MLUPS",
+                      "h2d_bytes_per_step": 24 * len(w.particles), "d2h_bytes_per_step": 48 * len(w.particles),
+                      "steps": e2e_steps}
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+    return res
+
+
+def secondary(args, world, local):
+    """The other workloads of the benchmark on the same GPU, each in its own
+    timed region: FP16 and BF16 offset storage of the 256x128x128 cell, the
+    512-lattice batch (FP32) and the 2,000-spheroid fibre suspension (FP32,
+    learned closure on with the trained parameters when they are present)."""
+    out = {}
+    w = workload("large")
+    for prec in ("f16", "bf16"):
+        r = measure(args, w, prec, world, local, min_region_s=0.5, steps=max(args.steps, 20))
+        out[f"storage_{prec}"] = summarise(r)
+    wb = workload("batched")
+    r = measure(args, wb, "f32", world, local, min_region_s=0.5, steps=max(args.steps // 4, 4))
+    out["batched"] = summarise(r)
+    wf = workload("fibre")
+    params = trained_closure()
+    r = measure(args, wf, "f32", world, local, closure_params=params, min_region_s=0.5,
+                steps=max(args.steps // 4, 4))
+    s = summarise(r)
+    s["closure"] = "trained" if params is not None else "off"
+    err = closure_error_record()
+    if err is not None:
+        s["force_torque_error"] = err
+    out["fibre"] = s
+    return out
+
+
+def summarise(r):
+    keep = ("workload", "prec", "cells", "fluid_cells", "particles", "ms_per_step", "reps", "steps_per_rep",
+            "mlups", "particle_steps_per_s", "launch")
+    s = {k: r[k] for k in keep}
+    s["mlups"] = round(s["mlups"], 1)
+    s["particle_steps_per_s"] = round(s["particle_steps_per_s"], 1)
+    s["ms_per_step"] = round(s["ms_per_step"], 5)
+    rf = r["roofline"]
+    s["roofline"] = {k: rf[k] for k in ("achieved", "peak", "frac", "avg_launch_ms", "bytes_per_launch",
+                                        "step_frac", "traffic")}
+    return s
+
+
+CLOSURE_PARAMS_FILE = os.path.join(ROOT, "paper_1503_06869_gb300", "closure", "params_fp16.npy")
+CLOSURE_EVAL_FILE = os.path.join(ROOT, "paper_1503_06869_gb300", "closure", "evaluation.json")
+
+
+def trained_closure():
+    if os.path.exists(CLOSURE_PARAMS_FILE):
+        return np.load(CLOSURE_PARAMS_FILE).astype(np.float16)
+    return None
+
+
+def closure_error_record():
+    """Held-out force/torque error of the coarse runs against the fine judge,
+    with and without the trained closure, as the training driver wrote it."""
+    if not os.path.exists(CLOSURE_EVAL_FILE):
+        return None
+    d = json.load(open(CLOSURE_EVAL_FILE))
+    return {k: d[k] for k in d if k in ("force_rms", "torque_rms", "units", "samples", "judge", "source")}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
-    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large", choices=["large", "small", "batched", "fibre"])
     ap.add_argument("--sequential", action="store_true",
                     help="batched workload: one context per lattice, stepped one after another")
     ap.add_argument("--closure", action="store_true",
-                    help="enable the learned force/torque closure (seeded small parameters)")
+                    help="enable the learned force/torque closure (trained parameters when present, else "
+                         "seeded small ones)")
     ap.add_argument("--prec", default="f32", choices=["f64", "f32", "f16", "bf16"])
     ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--min-region-s", type=float, default=1.0,
+                    help="repeat the K-step timed region until the repetitions cover this many seconds")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the FP16/BF16, batched and fibre-suspension lines of the default run")
     ap.add_argument("--launch", type=int, default=None,
                     help="fixed sweep block size (0 ring, -1 staged, 32..256 direct) instead of the autotuner's "
                          "choice; for profiling runs, where the profiler's serialisation skews the autotuner")
+    ap.add_argument("--cpt", type=int, default=None, help="with --launch: cells per thread of the direct sweep")
     ap.add_argument("--remap-fused", action="store_true",
                     help="run the re-mapping step as one cooperative launch instead of five launches")
     args = ap.parse_args()
@@ -299,114 +511,38 @@ def main():
         return run_sequential(args, w, rank, world)
 
     import torch
-    from paper_1503_06869_gb300 import lbm
     torch.cuda.set_device(local)
-    sim = lbm.Simulation(w.lattices, w.particles, prec=args.prec, device=local)
-    h = sim.h
+    params = None
     if args.closure:
-        # throughput only: the parameters are seeded and small, not trained
-        theta = np.random.default_rng(0).normal(size=lbm.CLOSURE_PARAMS) * 0.01
-        lbm.lbm_set_closure(h, theta.astype(np.float16))
-    if args.remap_fused:
-        lbm.lbm_set_remap_fused(h, True)
-    if args.launch is None:
-        lbm.lbm_autotune(h)
-    else:
-        lbm.lbm_set_launch(h, args.launch, 0)
-    info = lbm.lbm_get_info(h)
-    sim.step(args.warmup)
-    sim.sync()
-    nfluid = 0
-    for c, lat in enumerate(w.lattices[:1]):
-        f = lbm.lbm_get_fields(h, lat.ncells, c, rho=False, u=False, flags=True, pid=False)
-        nfluid = int((f["flags"] == 0).sum())
-    fluid_total = nfluid if len(w.lattices) == 1 else None
-
-    # --- timed region: K whole steps (CUDA-graph replay), inputs resident in
-    # HBM and larger than L2 -------------------------------------------------
+        params = trained_closure()
+        if params is None:
+            # throughput only: seeded small parameters
+            from paper_1503_06869_gb300 import lbm
+            params = (np.random.default_rng(0).normal(size=lbm.CLOSURE_PARAMS) * 0.01).astype(np.float16)
     clocks = ClockSampler(local)
     clocks.start()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    launches0 = lbm.lbm_get_launch_count(h)
-    barrier(world)
-    torch.cuda.synchronize()
-    ev0.record(sim.stream)
-    sim.step(args.steps)
-    ev1.record(sim.stream)
-    torch.cuda.synchronize()
-    barrier(world)
-    ms = ev0.elapsed_time(ev1)
+    r = measure(args, w, args.prec, world, local, launch=args.launch, cpt=args.cpt, closure_params=params,
+                clocks=clocks, min_region_s=args.min_region_s, e2e_steps=args.e2e_steps)
     clk = clocks.stop()
-    launches = lbm.lbm_get_launch_count(h) - launches0
-
-    # --- the sweep kernel alone: the same K steps again, each sweep launch
-    # bracketed by CUDA events on the context's stream (eager launches) -----
-    lbm.lbm_set_sweep_timing(h, True)
-    sim.step(args.steps)
-    sweep_ms, sweep_n = lbm.lbm_get_sweep_timing(h)
-    lbm.lbm_set_sweep_timing(h, False)
-    ms_max = max_over_ranks(ms, world)
-    cells = w.ncells
-    value = whole_job_rate(cells * args.steps, world, ms_max)
-
-    # roofline of the sweep kernel (dominant kernel): algorithmic bytes =
-    # 19 loads + 19 stores per fluid cell update
-    peak, peak_kind = measured_peaks()
-    bpp = BYTES_PER_POP[args.prec]
-    if fluid_total is None:
-        fluid_total = 0
-        for c, lat in enumerate(w.lattices):
-            f = lbm.lbm_get_fields(h, lat.ncells, c, rho=False, u=False, flags=True, pid=False)
-            fluid_total += int((f["flags"] == 0).sum())
-    bytes_per_launch = 38 * bpp * fluid_total
-    sweep_avg_ms = sweep_ms / max(sweep_n, 1)
-    achieved = bytes_per_launch / (sweep_avg_ms * 1e-3) / 1e9
-    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": sweep_traffic(w.name, args.prec),
-            "kernel": "sweep_kernel", "bytes_per_launch": bytes_per_launch,
-            "avg_launch_ms": round(sweep_avg_ms, 5), "peak_kind": f"{peak_kind} hbm_gbs"}
-
-    # --- end-to-end through the C interface with host buffers -------------
-    # every step: H2D of the particles' external loads from pinned memory,
-    # the step, D2H of the hydrodynamic force/torque (synchronising)
-    npart = max(len(w.particles), 1)
-    ext = torch.zeros((npart, 3), dtype=torch.float64).pin_memory()
-    Fh = torch.zeros((npart, 3), dtype=torch.float64).pin_memory()
-    Mh = torch.zeros((npart, 3), dtype=torch.float64).pin_memory()
-    extn, Fn, Mn = ext.numpy(), Fh.numpy(), Mh.numpy()
-    e2e_steps = args.e2e_steps
-    barrier(world)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        lbm.lbm_set_external(h, extn, None, len(w.particles))
-        lbm.lbm_step(h, 1)
-        lbm.lbm_get_forces(h, len(w.particles), Fn, Mn)
-    torch.cuda.synchronize()
-    t1 = time.perf_counter()
-    e2e_s = max_over_ranks(t1 - t0, world)
-    e2e_val = cells * e2e_steps * world / e2e_s / 1e6
-
-    line = {"metric": "MLUPS", "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 5),
+    line = {"metric": "MLUPS", "value": round(r["mlups"], 1), "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(r["ms_per_step"], 5),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.prec,
-            "data": "synthetic", "config": config_of(w, args, fluid_total),
-            "fluid_mlups": round(fluid_total * args.steps * world / (ms_max * 1e-3) / 1e6, 1),
-            "particle_steps_per_s": round(len(w.particles) * args.steps * world / (ms_max * 1e-3), 1),
-            "roofline": roof,
-            "e2e": {"value": round(e2e_val, 1), "unit": "MLUPS",
-                    "h2d_bytes_per_step": 24 * len(w.particles),
-                    "d2h_bytes_per_step": 48 * len(w.particles)},
-            "gpu_launches": int(launches),
-            "launch": {"block": info.sweep_block, "grid": info.sweep_grid, "split": bool(info.sweep_split),
-                       "remap_fused": bool(info.remap_fused), "remap_grid": info.remap_grid},
+            "data": "synthetic", "config": config_of(w, args, r["fluid_cells"]),
+            "timing": {"reps": r["reps"], "steps_per_rep": r["steps_per_rep"], "statistic": "median rep",
+                       "rep_ms_min": round(r["rep_ms_min"], 4), "rep_ms_max": round(r["rep_ms_max"], 4)},
+            "fluid_mlups": round(r["fluid_mlups"], 1),
+            "particle_steps_per_s": round(r["particle_steps_per_s"], 1),
+            "roofline": r["roofline"],
+            "e2e": r["e2e"],
+            "gpu_launches": r["launches_per_rep"],
+            "launch": r["launch"],
             "clocks": clk}
+    if world == 1 and not args.no_secondary and args.workload == "large" and args.launch is None:
+        line["secondary"] = secondary(args, world, local)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    sim.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

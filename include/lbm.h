@@ -31,6 +31,9 @@
  *  - Work is ordered on the stream given at creation.  lbm_step is
  *    asynchronous; calls that return host data synchronise that stream.
  *  - A context is used by one host thread at a time.
+ *  - A context belongs to the CUDA device that was current when it was
+ *    created; every call makes that device current for its duration and
+ *    restores the caller's device before returning.
  */
 #ifndef LBM_GB300_H
 #define LBM_GB300_H
@@ -66,7 +69,11 @@ typedef enum lbm_precision {
     LBM_F64 = 0,
     LBM_F32 = 1,
     LBM_F16_OFFSET = 2,   /* IEEE binary16 offsets, round to nearest even */
-    LBM_BF16_OFFSET = 3   /* bfloat16 offsets, round to nearest even */
+    LBM_BF16_OFFSET = 3   /* bfloat16 offsets; the sweep's stores round stochastically
+                           * (up with probability equal to the discarded fraction,
+                           * bits from a counter-based generator seeded by the cell
+                           * index and the step count: deterministic for a given
+                           * state and step), other stores to nearest even */
 } lbm_precision;
 
 /* Particle-id map codes of cells that are not particle cells. */
@@ -123,7 +130,11 @@ typedef struct lbm_grid_desc {
  * library; density is relative to rho0 = 1 units.  ext_force and ext_torque
  * are added to the hydrodynamic force and torque every step.  A fixed body
  * keeps its pose and velocities.  cell selects the lattice of a batch (0 for
- * a single lattice). */
+ * a single lattice).  Along a periodic axis of extent n a body must stay
+ * shorter than n/2 - 1 from its centre in every orientation (longest semi-axis
+ * a with 2a + 2 < n): the obstacle mapping and the surface velocity of a
+ * boundary link take the minimum image of the displacement from the centre,
+ * and for a longer body the two can pick different images. */
 #define LBM_SHAPE_ELLIPSOID 0
 #define LBM_SHAPE_SPHEROCYLINDER 1
 typedef struct lbm_particle {
@@ -176,8 +187,8 @@ lbm_status lbm_set_particles(lbm_ctx *ctx, const lbm_particle *p, int n);
  * was reported; LBM_ERR_CUDA. */
 lbm_status lbm_step(lbm_ctx *ctx, int nsteps);
 
-/* Wait for all queued work; reports LBM_ERR_NUMERIC (non-finite force or body
- * state), LBM_ERR_UNSUPPORTED (a body reached the fluid layer next to a
+/* Wait for all queued work; reports LBM_ERR_NUMERIC (non-finite force, body
+ * state or wall momentum), LBM_ERR_UNSUPPORTED (a body reached the fluid layer next to a
  * free-slip wall) or LBM_ERR_TIMEOUT (a bounded device wait ran out) if met
  * since the last check; the context then refuses further steps. */
 lbm_status lbm_sync(lbm_ctx *ctx);
@@ -256,6 +267,8 @@ typedef struct lbm_info {
     int sweep_split;            /* 1: the direct sweep runs split (lbm_set_sweep_split) */
     int remap_fused;            /* 1: the re-mapping step runs as one cooperative launch */
     int remap_grid;             /* blocks of that launch (0 when not fused) */
+    int cells_per_thread;       /* direct sweep: consecutive cells per thread (1, 2, 4) */
+    int device;                 /* CUDA device of the context */
 } lbm_info;
 
 lbm_status lbm_get_info(lbm_ctx *ctx, lbm_info *info);
@@ -271,6 +284,18 @@ lbm_status lbm_get_info(lbm_ctx *ctx, lbm_info *info);
  * effect at the next lbm_step.  Any other block value returns LBM_ERR_ARG.
  * The default is the direct sweep with 128 threads. */
 lbm_status lbm_set_launch(lbm_ctx *ctx, int block, int grid);
+
+/* Consecutive cells per thread of the direct sweep: 1, 2 or 4 (FP64 storage:
+ * 1 or 2).  With 2 or 4 a thread loads all its cells' populations before
+ * colliding any of them (more bytes in flight per thread) and moves the
+ * values of one population plane for its cells with one vector access
+ * wherever they are contiguous and aligned (every plane on even steps; on odd
+ * steps the planes of directions without an x component, when nx is a
+ * multiple of the group size); a direct-sweep tile then covers block * cpt
+ * cells.  Results are identical for every setting.  Default 1; the autotuner
+ * chooses.  Takes effect at the next lbm_step.  Errors: LBM_ERR_ARG for any
+ * other value. */
+lbm_status lbm_set_cells_per_thread(lbm_ctx *ctx, int cpt);
 
 /* Split direct sweep (enable != 0): near-obstacle cells (those next to a
  * body or a resting wall) leave the sweep kernel; a list kernel compacts them
@@ -295,6 +320,14 @@ lbm_status lbm_set_sweep_split(lbm_ctx *ctx, int enable);
  * effect at the next lbm_step. */
 lbm_status lbm_set_remap_fused(lbm_ctx *ctx, int enable);
 
+/* Poll limit of the bounded device-side waits of the fused re-mapping step
+ * (its grid barriers): a waiting block gives up after `polls` polls, sets the
+ * timeout condition and returns; 0 restores the default (2^20 polls, far
+ * above any wait of a resident launch).  A small limit makes such waits run
+ * out: the next synchronising call reports LBM_ERR_TIMEOUT and the context
+ * refuses further steps.  For tests of that path; synchronises the stream. */
+lbm_status lbm_set_wait_limit(lbm_ctx *ctx, unsigned polls);
+
 /* Momentum stabilisation (Sec. 4.1; enable != 0; default 0): before every
  * sweep the mean velocity ubar = sum(j) / (rho0 N_fluid) over all fluid cells
  * of the current state is computed (two extra launches per step, one read of
@@ -306,8 +339,11 @@ lbm_status lbm_set_remap_fused(lbm_ctx *ctx, int enable);
 lbm_status lbm_set_momentum_stabilisation(lbm_ctx *ctx, int enable);
 
 /* Choose the sweep launch shape by timing candidates on this context (runs
- * sweeps on scratch copies: the state is restored afterwards).  The chosen
- * shape is kept and returned through block/grid (either may be NULL). */
+ * sweeps on scratch copies: the state is restored afterwards): the ring and
+ * staged sweeps and the direct sweep with 128 or 256 threads, 1, 2 or 4 cells
+ * per thread, fused or split, on persistent and one-tile-per-block grids.
+ * The chosen shape is kept and returned through block/grid (either may be
+ * NULL); lbm_get_info reports the cells per thread and the split. */
 lbm_status lbm_autotune(lbm_ctx *ctx, int *block, int *grid);
 
 /* CUDA graphs: when enabled, lbm_step replays a captured two-step graph for

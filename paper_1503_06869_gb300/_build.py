@@ -18,7 +18,8 @@ OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "liblbm_gb300.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["lbm_sweep.cu", "lbm_particles.cu", "lbm_closure.cu", "lbm_api.cu", "lbm_sbf.cu"]
+SOURCES = ["lbm_sweep_f64.cu", "lbm_sweep_f32.cu", "lbm_sweep_f16.cu", "lbm_sweep_bf16.cu", "lbm_sweep.cu",
+           "lbm_particles.cu", "lbm_closure.cu", "lbm_api.cu", "lbm_sbf.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",
               "--expt-relaxed-constexpr", "-I", INCLUDE]

@@ -21,6 +21,7 @@ using namespace lbm;
 
 struct lbm_ctx {
     lbm_precision prec = LBM_F32;
+    int device = 0;                 // CUDA device current at creation; every call runs with it current
     int esize = 4;
     cudaStream_t stream = nullptr;
     void *(*dev_alloc)(size_t, void *) = nullptr;
@@ -47,6 +48,7 @@ struct lbm_ctx {
     __half *cl_par = nullptr;       // learned closure: FP16 network parameters
     bool closure = false;
     uint32_t *err = nullptr;
+    uint32_t *tick = nullptr;       // step counter (advanced by the rigid-body kernel)
 
     int np = 0;
     PartDev P{};
@@ -61,6 +63,7 @@ struct lbm_ctx {
     long long t = 0;
     int variant = SWEEP_DIRECT;     // sweep kernel variant
     int block = 128, grid = 0, ntiles = 0;
+    int cpt = 1;                    // direct sweep: consecutive cells per thread (1, 2, 4)
     int remap_bpb = 8;
     // fused re-mapping step: launch form found by the probe (-1 not probed,
     // 0 unavailable, 1 cooperative, 2 cooperative + programmatic dependency),
@@ -94,6 +97,23 @@ struct lbm_ctx {
 };
 
 namespace {
+
+// Makes the context's device current for the duration of a call and restores
+// the caller's device afterwards (every entry point that takes a context).
+struct DevGuard {
+    int prev = -1;
+    explicit DevGuard(const lbm_ctx *c) {
+        if (!c) return;
+        int cur = -1;
+        if (cudaGetDevice(&cur) == cudaSuccess && cur != c->device && cudaSetDevice(c->device) == cudaSuccess)
+            prev = cur;
+    }
+    ~DevGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+    DevGuard(const DevGuard &) = delete;
+    DevGuard &operator=(const DevGuard &) = delete;
+};
 
 lbm_status fail(lbm_ctx *c, lbm_status s, const std::string &m) {
     if (c) c->msg = m;
@@ -171,7 +191,7 @@ lbm_status check_desc(const lbm_grid_desc *d, std::string &m) {
     return LBM_OK;
 }
 
-int tile_cells(const lbm_ctx *ctx) { return ctx->variant == SWEEP_DIRECT ? ctx->block : STAGED_TILE; }
+int tile_cells(const lbm_ctx *ctx) { return ctx->variant == SWEEP_DIRECT ? ctx->block * ctx->cpt : STAGED_TILE; }
 
 void fill_tiles(lbm_ctx *ctx) {
     int tile = 0;
@@ -188,7 +208,7 @@ int default_grid(lbm_ctx *ctx) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int nb = sweep_max_active_blocks(ctx->prec, ctx->variant, ctx->block);
+    int nb = sweep_max_active_blocks(ctx->prec, ctx->variant, ctx->block, ctx->cpt);
     if (nb <= 0) nb = 1;
     long long g = (long long)sms * nb;
     if (g > ctx->ntiles) g = ctx->ntiles;
@@ -211,6 +231,7 @@ SweepArgs sweep_args(lbm_ctx *ctx) {
     a.tile_lat = ctx->tile_lat;
     a.links = ctx->links;
     a.nbody = ctx->nbody;
+    a.tick = ctx->tick;
     const bool split = ctx->split && ctx->variant == SWEEP_DIRECT;
     a.near_list = split ? ctx->near_list : nullptr;
     a.near_count = split ? ctx->near_count : nullptr;
@@ -251,6 +272,7 @@ RemapArgs remap_args(lbm_ctx *ctx) {
     a.tile = tile_cells(ctx);
     a.links = ctx->links;
     a.nbody = ctx->nbody;
+    a.tick = ctx->tick;
     return a;
 }
 
@@ -319,7 +341,7 @@ lbm_status enqueue_step(lbm_ctx *ctx, bool timed) {
         }
         CK(cudaEventRecord(ctx->ev[ctx->ev_used], ctx->stream));
     }
-    CK(launch_sweep(ctx->prec, parity, ctx->variant, sa, ctx->grid, ctx->block, ctx->stream));
+    CK(launch_sweep(ctx->prec, parity, ctx->variant, sa, ctx->grid, ctx->block, ctx->cpt, ctx->stream));
     if (timed) {
         CK(cudaEventRecord(ctx->ev[ctx->ev_used + 1], ctx->stream));
         ctx->ev_used += 2;
@@ -423,7 +445,7 @@ lbm_status graph_step(lbm_ctx *ctx) {
 lbm_status eval_err_word(lbm_ctx *ctx, uint32_t e) {
     if (e & ERR_NONFINITE) {
         ctx->broken = true;
-        return fail(ctx, LBM_ERR_NUMERIC, "non-finite force, torque or particle state");
+        return fail(ctx, LBM_ERR_NUMERIC, "non-finite force, torque, particle state or wall momentum");
     }
     if (e & ERR_FSLIP_BODY) {
         ctx->broken = true;
@@ -457,14 +479,18 @@ void free_particles(lbm_ctx *ctx) {
     ctx->np = 0;
 }
 
+// One particle buffer; a failed allocation raises *failed (the buffers
+// allocated so far stay in part_bufs, so free_particles releases them).
 template <class T>
-T *part_alloc(lbm_ctx *ctx, size_t count) {
+T *part_alloc(lbm_ctx *ctx, size_t count, bool *failed) {
     size_t bytes = count * sizeof(T);
     if (bytes == 0) bytes = 16;
     void *p = dalloc(ctx, bytes);
     if (p) {
         ctx->part_bufs.push_back(p);
         ctx->owned.push_back(p);
+    } else {
+        *failed = true;
     }
     return static_cast<T *>(p);
 }
@@ -498,6 +524,11 @@ lbm_status create_common(const lbm_grid_desc *cells, int ncells, lbm_ctx **out) 
     }
     if ((cells[0].dev_alloc == nullptr) != (cells[0].dev_free == nullptr)) return LBM_ERR_ARG;
     lbm_ctx *ctx = new lbm_ctx();
+    if (cudaGetDevice(&ctx->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return LBM_ERR_CUDA;
+    }
     ctx->prec = cells[0].prec;
     ctx->esize = storage_bytes(ctx->prec);
     ctx->stream = (cudaStream_t)cells[0].cuda_stream;
@@ -555,6 +586,23 @@ lbm_status create_common(const lbm_grid_desc *cells, int ncells, lbm_ctx **out) 
             L.fwhi[a] = (float)L.whi[a];
         }
         for (int q = 0; q < Q; ++q) L.off[q] = cx(q) + cy(q) * d.nx + cz(q) * d.nx * d.ny;
+        {
+            // collision constants (see collide in the sweep)
+            const double om = L.omega, oo = L.omega_odd, r0 = L.rho0, w1 = 1.0 / 18.0, w2 = 1.0 / 36.0;
+            const double k[11] = {1.0 - om,           om / 3.0,           -1.5 * r0,          0.5 * (1.0 - om),
+                                  0.5 * (1.0 - oo),   om * w1,            om * w2,            4.5 * r0 * om * w1,
+                                  4.5 * r0 * om * w2, 3.0 * r0 * oo * w1, 3.0 * r0 * oo * w2};
+            for (int i = 0; i < 11; ++i) {
+                L.kd[i] = k[i];
+                L.kf[i] = (float)k[i];
+            }
+            for (int i = 0; i < 9; ++i) {
+                const int q = 2 * i + 1;
+                const double cg = cx(q) * d.body_force[0] + cy(q) * d.body_force[1] + cz(q) * d.body_force[2];
+                L.fsd[i] = 3.0 * wq(q) * r0 * cg;
+                L.fsf[i] = (float)L.fsd[i];
+            }
+        }
         foff += (long long)Q * L.npad;
         coff += (L.n + 255) / 256 * 256;
         // a shifted staging window reaches at most nx*ny + nx + 1 cells (plus one
@@ -580,6 +628,7 @@ lbm_status create_common(const lbm_grid_desc *cells, int ncells, lbm_ctx **out) 
     ctx->wall_acc = (double *)owned_alloc(ctx, sizeof(double) * 6 * ACC_COPIES * ncells);
     ctx->wall_last = (double *)owned_alloc(ctx, sizeof(double) * 6 * ncells);
     ctx->err = (uint32_t *)owned_alloc(ctx, 16);
+    ctx->tick = (uint32_t *)owned_alloc(ctx, 16);
     ctx->gbar = (GridBar *)owned_alloc(ctx, 16);
     ctx->stab_acc = (double *)owned_alloc(ctx, 64);
     ctx->stab_accf = (float *)owned_alloc(ctx, 16);
@@ -590,7 +639,7 @@ lbm_status create_common(const lbm_grid_desc *cells, int ncells, lbm_ctx **out) 
         if (ncells > 1) ctx->tile_lat = (int *)owned_alloc(ctx, sizeof(int) * (size_t)(tiles32 + 1));
     }
     if (!ctx->lat_d || !ctx->f || !ctx->flags || !ctx->pid || !ctx->pid_prev || !ctx->wall_acc ||
-        !ctx->wall_last || !ctx->err || !ctx->tbits || !ctx->links || !ctx->nbody || !ctx->near_list ||
+        !ctx->wall_last || !ctx->err || !ctx->tick || !ctx->tbits || !ctx->links || !ctx->nbody || !ctx->near_list ||
         !ctx->near_count || !ctx->gbar || !ctx->stab_acc || !ctx->stab_accf || (ncells > 1 && !ctx->tile_lat)) {
         lbm_destroy(ctx);
         return LBM_ERR_OOM;
@@ -608,6 +657,7 @@ lbm_status create_common(const lbm_grid_desc *cells, int ncells, lbm_ctx **out) 
         cudaMemsetAsync(ctx->wall_acc, 0, sizeof(double) * 6 * ACC_COPIES * ncells, ctx->stream) != cudaSuccess ||
         cudaMemsetAsync(ctx->wall_last, 0, sizeof(double) * 6 * ncells, ctx->stream) != cudaSuccess ||
         cudaMemsetAsync(ctx->err, 0, 16, ctx->stream) != cudaSuccess ||
+        cudaMemsetAsync(ctx->tick, 0, 16, ctx->stream) != cudaSuccess ||
         cudaMemsetAsync(ctx->gbar, 0, 16, ctx->stream) != cudaSuccess ||
         cudaMemsetAsync(ctx->stab_acc, 0, 64, ctx->stream) != cudaSuccess ||
         cudaMemsetAsync(ctx->stab_accf, 0, 16, ctx->stream) != cudaSuccess) {
@@ -644,6 +694,7 @@ lbm_status lbm_create_batch(const lbm_grid_desc *cells, int ncells, lbm_ctx **ou
 
 lbm_status lbm_destroy(lbm_ctx *ctx) {
     if (!ctx) return LBM_ERR_ARG;
+    DevGuard dg(ctx);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     drop_graph(ctx);
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
@@ -671,6 +722,7 @@ const char *lbm_status_string(lbm_status s) {
 
 lbm_status lbm_set_particles(lbm_ctx *ctx, const lbm_particle *p, int n) {
     if (!ctx) return LBM_ERR_ARG;
+    DevGuard dg(ctx);
     if (n < 0 || (n > 0 && !p)) return fail(ctx, LBM_ERR_ARG, "bad particle array");
     // validate and derive host-side quantities
     std::vector<double> pos(3 * n), quat(4 * n), vel(3 * n), om(3 * n), L(3 * n), semi(3 * n), mass(n),
@@ -803,36 +855,45 @@ lbm_status lbm_set_particles(lbm_ctx *ctx, const lbm_particle *p, int n) {
     PartDev &P = ctx->P;
     P.np = n;
     const size_t m = n > 0 ? n : 1;
-    P.pos = part_alloc<double>(ctx, 3 * m);
-    P.quat = part_alloc<double>(ctx, 4 * m);
-    P.vel = part_alloc<double>(ctx, 3 * m);
-    P.om = part_alloc<double>(ctx, 3 * m);
-    P.L = part_alloc<double>(ctx, 3 * m);
-    P.semi = part_alloc<double>(ctx, 3 * m);
-    P.mass = part_alloc<double>(ctx, m);
-    P.inertia = part_alloc<double>(ctx, 3 * m);
-    P.minv = part_alloc<double>(ctx, m);
-    P.Iinv = part_alloc<double>(ctx, 3 * m);
-    P.bodyf = part_alloc<float>(ctx, BF_STRIDE * m);
-    P.R64 = part_alloc<double>(ctx, 9 * m);
-    P.feat = part_alloc<float>(ctx, (size_t)CL_IN * m);
-    P.extF = part_alloc<double>(ctx, 3 * m);
-    P.extM = part_alloc<double>(ctx, 3 * m);
-    P.cell = part_alloc<int>(ctx, m);
-    P.fixed = part_alloc<int>(ctx, m);
-    P.pos_old = part_alloc<double>(ctx, 3 * m);
-    P.vel_old = part_alloc<double>(ctx, 3 * m);
-    P.om_old = part_alloc<double>(ctx, 3 * m);
-    P.quat_old = part_alloc<double>(ctx, 4 * m);
-    P.acc = part_alloc<double>(ctx, 6 * ACC_COPIES * m);
-    P.last = part_alloc<double>(ctx, 6 * m);
-    P.region = part_alloc<int>(ctx, 6 * m);
-    P.changed = part_alloc<int>(ctx, m);
-    for (void *b : ctx->part_bufs)
-        if (!b) {
-            free_particles(ctx);
-            return fail(ctx, LBM_ERR_OOM, "particle buffers");
+    bool failed = false;
+    P.pos = part_alloc<double>(ctx, 3 * m, &failed);
+    P.quat = part_alloc<double>(ctx, 4 * m, &failed);
+    P.vel = part_alloc<double>(ctx, 3 * m, &failed);
+    P.om = part_alloc<double>(ctx, 3 * m, &failed);
+    P.L = part_alloc<double>(ctx, 3 * m, &failed);
+    P.semi = part_alloc<double>(ctx, 3 * m, &failed);
+    P.mass = part_alloc<double>(ctx, m, &failed);
+    P.inertia = part_alloc<double>(ctx, 3 * m, &failed);
+    P.minv = part_alloc<double>(ctx, m, &failed);
+    P.Iinv = part_alloc<double>(ctx, 3 * m, &failed);
+    P.bodyf = part_alloc<float>(ctx, BF_STRIDE * m, &failed);
+    P.R64 = part_alloc<double>(ctx, 9 * m, &failed);
+    P.feat = part_alloc<float>(ctx, (size_t)CL_IN * m, &failed);
+    P.extF = part_alloc<double>(ctx, 3 * m, &failed);
+    P.extM = part_alloc<double>(ctx, 3 * m, &failed);
+    P.cell = part_alloc<int>(ctx, m, &failed);
+    P.fixed = part_alloc<int>(ctx, m, &failed);
+    P.pos_old = part_alloc<double>(ctx, 3 * m, &failed);
+    P.vel_old = part_alloc<double>(ctx, 3 * m, &failed);
+    P.om_old = part_alloc<double>(ctx, 3 * m, &failed);
+    P.quat_old = part_alloc<double>(ctx, 4 * m, &failed);
+    P.acc = part_alloc<double>(ctx, 6 * ACC_COPIES * m, &failed);
+    P.last = part_alloc<double>(ctx, 6 * m, &failed);
+    P.region = part_alloc<int>(ctx, 6 * m, &failed);
+    P.changed = part_alloc<int>(ctx, m, &failed);
+    if (failed) {
+        // the previous bodies' cells are still mapped: map the lattices
+        // without bodies, so that the context stays consistent (and usable)
+        free_particles(ctx);
+        if (n > 0) {
+            const std::string keep = "particle buffers: device allocation failed";
+            lbm_status s0 = lbm_set_particles(ctx, nullptr, 0);
+            if (s0 != LBM_OK) ctx->broken = true;
+            return fail(ctx, LBM_ERR_OOM, keep);
         }
+        ctx->broken = true;
+        return fail(ctx, LBM_ERR_OOM, "particle buffers: device allocation failed");
+    }
     ctx->np = n;
     if (ctx->host_stage) cudaFreeHost(ctx->host_stage);
     ctx->host_stage = nullptr;
@@ -883,6 +944,7 @@ lbm_status lbm_set_particles(lbm_ctx *ctx, const lbm_particle *p, int n) {
 
 lbm_status lbm_step(lbm_ctx *ctx, int nsteps) {
     if (!ctx) return LBM_ERR_ARG;
+    DevGuard dg(ctx);
     if (nsteps < 0) return fail(ctx, LBM_ERR_ARG, "nsteps < 0");
     if (ctx->broken) return fail(ctx, LBM_ERR_STATE, "context stopped after an earlier error");
     int left = nsteps;
@@ -933,12 +995,14 @@ lbm_status lbm_step(lbm_ctx *ctx, int nsteps) {
 
 lbm_status lbm_sync(lbm_ctx *ctx) {
     if (!ctx) return LBM_ERR_ARG;
+    DevGuard dg(ctx);
     CK(cudaStreamSynchronize(ctx->stream));
     return check_err_word(ctx);
 }
 
 lbm_status lbm_get_forces(lbm_ctx *ctx, double *force3n, double *torque3n, int n) {
     if (!ctx) return LBM_ERR_ARG;
+    DevGuard dg(ctx);
     if (n < 0 || n > ctx->np) return fail(ctx, LBM_ERR_ARG, "n out of range");
     if (n == 0) return LBM_OK;
     // forces and the error word into pinned memory, one synchronisation
@@ -957,6 +1021,7 @@ lbm_status lbm_get_forces(lbm_ctx *ctx, double *force3n, double *torque3n, int n
 
 lbm_status lbm_get_wall_forces(lbm_ctx *ctx, int cell, double *f6) {
     if (!ctx || !f6) return LBM_ERR_ARG;
+    DevGuard dg(ctx);
     if (cell < 0 || cell >= ctx->nlat) return fail(ctx, LBM_ERR_ARG, "cell out of range");
     CK(cudaMemcpyAsync(f6, ctx->wall_last + 6 * cell, sizeof(double) * 6, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -965,6 +1030,7 @@ lbm_status lbm_get_wall_forces(lbm_ctx *ctx, int cell, double *f6) {
 
 lbm_status lbm_get_particles(lbm_ctx *ctx, lbm_particle *p, int n) {
     if (!ctx || (n > 0 && !p)) return LBM_ERR_ARG;
+    DevGuard dg(ctx);
     if (n < 0 || n > ctx->np) return fail(ctx, LBM_ERR_ARG, "n out of range");
     if (n == 0) return LBM_OK;
     std::vector<double> pos(3 * n), quat(4 * n), vel(3 * n), om(3 * n), semi(3 * n), mass(n), eF(3 * n), eM(3 * n);
@@ -1002,6 +1068,7 @@ lbm_status lbm_get_particles(lbm_ctx *ctx, lbm_particle *p, int n) {
 
 lbm_status lbm_set_external(lbm_ctx *ctx, const double *force3n, const double *torque3n, int n) {
     if (!ctx) return LBM_ERR_ARG;
+    DevGuard dg(ctx);
     if (n < 0 || n > ctx->np) return fail(ctx, LBM_ERR_ARG, "n out of range");
     if (n == 0) return LBM_OK;
     if (force3n) CK(cudaMemcpyAsync(ctx->P.extF, force3n, 24 * n, cudaMemcpyHostToDevice, ctx->stream));
@@ -1013,6 +1080,7 @@ lbm_status lbm_set_external(lbm_ctx *ctx, const double *force3n, const double *t
 lbm_status lbm_get_fields(lbm_ctx *ctx, int cell, double *rho, double *u3, uint8_t *flags, uint32_t *pid,
                           double *pdfs) {
     if (!ctx) return LBM_ERR_ARG;
+    DevGuard dg(ctx);
     if (cell < 0 || cell >= ctx->nlat) return fail(ctx, LBM_ERR_ARG, "cell out of range");
     const LatDev &h = ctx->lat_h[cell];
     const size_t n = h.n;
@@ -1044,6 +1112,7 @@ lbm_status lbm_get_fields(lbm_ctx *ctx, int cell, double *rho, double *u3, uint8
 
 lbm_status lbm_set_pdfs(lbm_ctx *ctx, int cell, const double *pdfs) {
     if (!ctx || !pdfs) return LBM_ERR_ARG;
+    DevGuard dg(ctx);
     if (cell < 0 || cell >= ctx->nlat) return fail(ctx, LBM_ERR_ARG, "cell out of range");
     const LatDev &h = ctx->lat_h[cell];
     const size_t bytes = 8 * Q * (size_t)h.n;
@@ -1079,7 +1148,8 @@ std::mutex g_links_scratch_mu;
 int *g_links_scratch_addr[MAX_DEVICES] = {};
 
 // Device address of g_links_scratch on the current device (looked up on the
-// first call for that device).
+// first call for that device).  Every entry point runs with its context's
+// device current, so this is the address on the context's device.
 cudaError_t links_scratch_address(int **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1103,6 +1173,7 @@ extern "C" {
 lbm_status lbm_get_links_noalloc(lbm_ctx *ctx, int cell, int32_t *d_idx, int8_t *d_q, uint32_t *d_pid, int cap,
                                  int *d_count) {
     if (!ctx || !d_count || cap < 0) return LBM_ERR_ARG;
+    DevGuard dg(ctx);
     if (cell < 0 || cell >= ctx->nlat) return fail(ctx, LBM_ERR_ARG, "cell out of range");
     const LatDev &h = ctx->lat_h[cell];
     const int nblocks = (h.n + 255) / 256;
@@ -1121,6 +1192,7 @@ lbm_status lbm_get_links_noalloc(lbm_ctx *ctx, int cell, int32_t *d_idx, int8_t 
 
 lbm_status lbm_get_links(lbm_ctx *ctx, int cell, int32_t *idx, int8_t *q, uint32_t *pid, int cap, int *count) {
     if (!ctx || !count || cap < 0) return LBM_ERR_ARG;
+    DevGuard dg(ctx);
     if (cell < 0 || cell >= ctx->nlat) return fail(ctx, LBM_ERR_ARG, "cell out of range");
     const LatDev &h = ctx->lat_h[cell];
     const int nblocks = (h.n + 255) / 256;
@@ -1152,6 +1224,7 @@ lbm_status lbm_get_links(lbm_ctx *ctx, int cell, int32_t *idx, int8_t *q, uint32
 
 lbm_status lbm_get_info(lbm_ctx *ctx, lbm_info *info) {
     if (!ctx || !info) return LBM_ERR_ARG;
+    DevGuard dg(ctx);
     long long n = 0;
     for (auto &L : ctx->lat_h) n += L.n;
     info->ncells_total = n;
@@ -1166,11 +1239,14 @@ lbm_status lbm_get_info(lbm_ctx *ctx, lbm_info *info) {
     info->sweep_split = (ctx->split && ctx->variant == SWEEP_DIRECT) ? 1 : 0;
     info->remap_fused = fused_remap(ctx) ? 1 : 0;
     info->remap_grid = fused_remap(ctx) ? ctx->remap_grid : 0;
+    info->cells_per_thread = ctx->variant == SWEEP_DIRECT ? ctx->cpt : 1;
+    info->device = ctx->device;
     return LBM_OK;
 }
 
 lbm_status lbm_set_launch(lbm_ctx *ctx, int block, int grid) {
     if (!ctx) return LBM_ERR_ARG;
+    DevGuard dg(ctx);
     if (block != 0 && block != -1 && (block < 32 || block > 256 || block % 32))
         return fail(ctx, LBM_ERR_ARG, "block must be 0 (ring sweep), -1 (staged sweep) or a multiple of 32 in [32, 256]");
     CK(cudaStreamSynchronize(ctx->stream));
@@ -1187,8 +1263,27 @@ lbm_status lbm_set_launch(lbm_ctx *ctx, int block, int grid) {
     return LBM_OK;
 }
 
+lbm_status lbm_set_cells_per_thread(lbm_ctx *ctx, int cpt) {
+    if (!ctx) return LBM_ERR_ARG;
+    DevGuard dg(ctx);
+    if (!sweep_cpt_supported(ctx->prec, cpt))
+        return fail(ctx, LBM_ERR_ARG, "cells per thread must be 1, 2 or 4 (1 or 2 for FP64 storage)");
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->cpt = cpt;
+    fill_tiles(ctx);
+    lbm_status s = upload_lattices(ctx);
+    if (s != LBM_OK) return s;
+    ctx->grid = default_grid(ctx);
+    drop_graph(ctx);
+    s = recount_tiles(ctx);  // the tile size changes with the cells per thread
+    if (s != LBM_OK) return s;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+}
+
 lbm_status lbm_autotune(lbm_ctx *ctx, int *block_out, int *grid_out) {
     if (!ctx) return LBM_ERR_ARG;
+    DevGuard dg(ctx);
     CK(cudaStreamSynchronize(ctx->stream));
     // back up the populations; sweeps below run on the live buffers
     const size_t fbytes = (size_t)ctx->f_elems * ctx->esize;
@@ -1199,22 +1294,31 @@ lbm_status lbm_autotune(lbm_ctx *ctx, int *block_out, int *grid_out) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     // candidates: the ring sweep (block 0), the staged sweep (block -1) and
-    // the direct sweep at two block sizes, fused or split, each with
-    // persistent grids (1x, 2x resident) and one tile per block
-    const int blocks[] = {0, -1, 128, 256, 128 + 1024, 256 + 1024};  // +1024: split direct sweep
+    // the direct sweep at two block sizes with 1, 2 or 4 cells per thread,
+    // fused or split, each with persistent grids (1x, 2x resident) and one
+    // tile per block
+    struct Cand {
+        int block, cpt;
+        bool split;
+    };
+    std::vector<Cand> cands = {{0, 1, false}, {-1, 1, false}};
+    for (int blk : {128, 256})
+        for (int c : {1, 2, 4})
+            if (sweep_cpt_supported(ctx->prec, c))
+                for (bool sp : {false, true}) cands.push_back({blk, c, sp});
     double best = 1e30;
     int bb = ctx->variant == SWEEP_RING ? 0 : (ctx->variant == SWEEP_STAGED ? -1 : ctx->block);
-    int bg = ctx->grid;
+    int bg = ctx->grid, bc = ctx->cpt;
     bool bsplit = ctx->split;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    for (int cand : blocks) {
-        const int blk = cand > 1024 ? cand - 1024 : cand;
-        lbm_status s = lbm_set_launch(ctx, blk, 0);
+    for (const Cand &cand : cands) {
+        ctx->cpt = cand.cpt;
+        lbm_status s = lbm_set_launch(ctx, cand.block, 0);
         if (s != LBM_OK) break;
-        ctx->split = cand > 1024;
-        const int occ = sweep_max_active_blocks(ctx->prec, ctx->variant, ctx->block);
+        ctx->split = cand.split;
+        const int occ = sweep_max_active_blocks(ctx->prec, ctx->variant, ctx->block, ctx->cpt);
         if (occ <= 0) continue;
         const int grids[] = {sms * occ, 2 * sms * occ, ctx->ntiles};
         for (int gr : grids) {
@@ -1222,14 +1326,14 @@ lbm_status lbm_autotune(lbm_ctx *ctx, int *block_out, int *grid_out) {
             ctx->grid = gr;
             SweepArgs sa = sweep_args(ctx);
             for (int w = 0; w < 2; ++w) {
-                CK(launch_sweep(ctx->prec, 0, ctx->variant, sa, gr, ctx->block, ctx->stream));
-                CK(launch_sweep(ctx->prec, 1, ctx->variant, sa, gr, ctx->block, ctx->stream));
+                CK(launch_sweep(ctx->prec, 0, ctx->variant, sa, gr, ctx->block, ctx->cpt, ctx->stream));
+                CK(launch_sweep(ctx->prec, 1, ctx->variant, sa, gr, ctx->block, ctx->cpt, ctx->stream));
             }
             CK(cudaEventRecord(e0, ctx->stream));
             const int reps = 4;
             for (int r = 0; r < reps; ++r) {
-                CK(launch_sweep(ctx->prec, 0, ctx->variant, sa, gr, ctx->block, ctx->stream));
-                CK(launch_sweep(ctx->prec, 1, ctx->variant, sa, gr, ctx->block, ctx->stream));
+                CK(launch_sweep(ctx->prec, 0, ctx->variant, sa, gr, ctx->block, ctx->cpt, ctx->stream));
+                CK(launch_sweep(ctx->prec, 1, ctx->variant, sa, gr, ctx->block, ctx->cpt, ctx->stream));
             }
             CK(cudaEventRecord(e1, ctx->stream));
             CK(cudaEventSynchronize(e1));
@@ -1238,8 +1342,9 @@ lbm_status lbm_autotune(lbm_ctx *ctx, int *block_out, int *grid_out) {
             CK(cudaEventElapsedTime(&ms, e0, e1));
             if (ms < best) {
                 best = ms;
-                bb = blk;
+                bb = cand.block;
                 bg = gr;
+                bc = cand.cpt;
                 bsplit = ctx->split;
             }
         }
@@ -1247,6 +1352,7 @@ lbm_status lbm_autotune(lbm_ctx *ctx, int *block_out, int *grid_out) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     ctx->split = bsplit;
+    ctx->cpt = bb > 0 ? bc : 1;
     lbm_status s = lbm_set_launch(ctx, bb, bg);
     CK(cudaMemcpyAsync(ctx->f, backup, fbytes, cudaMemcpyDeviceToDevice, ctx->stream));
     if (ctx->np > 0) CK(cudaMemsetAsync(ctx->P.acc, 0, sizeof(double) * 6 * ACC_COPIES * ctx->np, ctx->stream));
@@ -1260,6 +1366,7 @@ lbm_status lbm_autotune(lbm_ctx *ctx, int *block_out, int *grid_out) {
 
 lbm_status lbm_set_sweep_split(lbm_ctx *ctx, int enable) {
     if (!ctx) return LBM_ERR_ARG;
+    DevGuard dg(ctx);
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->split = enable != 0;
     drop_graph(ctx);
@@ -1268,6 +1375,7 @@ lbm_status lbm_set_sweep_split(lbm_ctx *ctx, int enable) {
 
 lbm_status lbm_set_momentum_stabilisation(lbm_ctx *ctx, int enable) {
     if (!ctx) return LBM_ERR_ARG;
+    DevGuard dg(ctx);
     if (ctx->nlat != 1) return fail(ctx, LBM_ERR_UNSUPPORTED, "momentum stabilisation needs a single lattice");
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->stab = enable != 0;
@@ -1282,6 +1390,7 @@ lbm_status lbm_set_momentum_stabilisation(lbm_ctx *ctx, int enable) {
 
 lbm_status lbm_set_remap_fused(lbm_ctx *ctx, int enable) {
     if (!ctx) return LBM_ERR_ARG;
+    DevGuard dg(ctx);
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->remap_fused = enable != 0;
     update_remap_grid(ctx);
@@ -1289,8 +1398,18 @@ lbm_status lbm_set_remap_fused(lbm_ctx *ctx, int enable) {
     return LBM_OK;
 }
 
+lbm_status lbm_set_wait_limit(lbm_ctx *ctx, unsigned polls) {
+    if (!ctx) return LBM_ERR_ARG;
+    DevGuard dg(ctx);
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpyAsync(&ctx->gbar->limit, &polls, sizeof(unsigned), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+}
+
 lbm_status lbm_set_graphs(lbm_ctx *ctx, int enable) {
     if (!ctx) return LBM_ERR_ARG;
+    DevGuard dg(ctx);
     ctx->graphs = enable != 0 && ctx->stream != nullptr;
     if (!ctx->graphs) drop_graph(ctx);
     return LBM_OK;
@@ -1298,6 +1417,7 @@ lbm_status lbm_set_graphs(lbm_ctx *ctx, int enable) {
 
 lbm_status lbm_set_sweep_timing(lbm_ctx *ctx, int enable) {
     if (!ctx) return LBM_ERR_ARG;
+    DevGuard dg(ctx);
     lbm_status s = harvest_timing(ctx);
     if (s != LBM_OK) return s;
     ctx->timing = enable != 0;
@@ -1308,6 +1428,7 @@ lbm_status lbm_set_sweep_timing(lbm_ctx *ctx, int enable) {
 
 lbm_status lbm_get_sweep_timing(lbm_ctx *ctx, double *ms, long long *launches) {
     if (!ctx) return LBM_ERR_ARG;
+    DevGuard dg(ctx);
     lbm_status s = harvest_timing(ctx);
     if (s != LBM_OK) return s;
     if (ms) *ms = ctx->ms_acc;
@@ -1319,12 +1440,14 @@ lbm_status lbm_get_sweep_timing(lbm_ctx *ctx, double *ms, long long *launches) {
 
 lbm_status lbm_get_launch_count(lbm_ctx *ctx, long long *launches) {
     if (!ctx || !launches) return LBM_ERR_ARG;
+    DevGuard dg(ctx);
     *launches = ctx->launches;
     return LBM_OK;
 }
 
 lbm_status lbm_set_closure(lbm_ctx *ctx, const void *params, size_t bytes) {
     if (!ctx) return LBM_ERR_ARG;
+    DevGuard dg(ctx);
     CK(cudaStreamSynchronize(ctx->stream));
     drop_graph(ctx);  // the captured step changes with the closure
     if (!params) {
@@ -1345,6 +1468,7 @@ lbm_status lbm_set_closure(lbm_ctx *ctx, const void *params, size_t bytes) {
 
 lbm_status lbm_closure_features(lbm_ctx *ctx, float *features, int n) {
     if (!ctx) return LBM_ERR_ARG;
+    DevGuard dg(ctx);
     if (n != ctx->np || (n > 0 && !features)) return fail(ctx, LBM_ERR_ARG, "n must equal the number of bodies");
     if (n == 0) return LBM_OK;
     CK(launch_closure_features(ctx->prec, (int)(ctx->t & 1), closure_args(ctx), ctx->stream));

@@ -96,6 +96,13 @@ struct LatDev {
     // y walls (0 without them: no closure) and dynamic viscosity
     float cl_gamma, cl_mu;
     int off[Q];            // linear offset of x + c_q for cells off the periodic faces
+    // TRT collision constants (Eqs. TRTOp, EqPDF_TRT regrouped, see collide):
+    // kd / kf = {1 - om, om w_0, -1.5 rho0, (1 - om)/2, (1 - oo)/2, om w_1,
+    // om w_2, 4.5 rho0 om w_1, 4.5 rho0 om w_2, 3 rho0 oo w_1, 3 rho0 oo w_2}
+    // (w_1 = 1/18 axis, w_2 = 1/36 diagonal directions), and per direction
+    // pair i (q = 2i + 1) the body-force source 3 w_q rho0 c_q.g
+    double kd[11], fsd[9];
+    float kf[11], fsf[9];
     // momentum stabilisation (Sec. 4.1): mean fluid velocity of the current
     // step, subtracted from u in every equilibrium; null when off
     const double *ubar;
@@ -172,7 +179,54 @@ struct SweepArgs {
     uint32_t *near_list;
     uint32_t *near_count;
     const int *tile_lat;     // batches: lattice of every tile (null: binary search on tile0)
+    const uint32_t *tick;    // step counter (seed of the BF16 stochastic rounding)
 };
+
+// Stochastic rounding of the BF16 sweep stores.  A bfloat16 keeps 8
+// significant bits; rounded to nearest, a population that changes little from
+// step to step gets the same rounding error every step, and on flows that are
+// uniform along whole planes (shear between walls) that error is the same over
+// the plane, a steady bias that the flow integrates.  The sweep's BF16 stores
+// therefore round up with probability equal to the discarded fraction of the
+// FP32 value (unbiased), driven by a counter-based generator: a per-step seed
+// from the context's step counter (advanced by the rigid-body kernel), hashed
+// with the cell index by Wellons' "lowbias32" integer hash, then one step of
+// the Numerical Recipes linear congruential generator per stored population,
+// whose upper 16 bits are the rounding bits.  Deterministic for a given state
+// and step; FP16, FP32 and FP64 stores round to nearest even.
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+// Per-step seed from the step counter (null: 0).
+__device__ __forceinline__ uint32_t step_seed(const uint32_t *tick) {
+    return tick ? mix32(*tick * 0x9e3779b9u + 0x632be5abu) : 0u;
+}
+template <int PREC> struct Rnd {
+    __device__ __forceinline__ Rnd(uint32_t, long long) {}
+    __device__ __forceinline__ uint32_t next() { return 0u; }
+};
+template <> struct Rnd<LBM_BF16_OFFSET> {
+    uint32_t s;
+    __device__ __forceinline__ Rnd(uint32_t seed, long long cell) : s(mix32(seed ^ (uint32_t)cell)) {}
+    __device__ __forceinline__ uint32_t next() {
+        s = s * 1664525u + 1013904223u;
+        return s >> 16;
+    }
+};
+// FP32 -> BF16 bits, rounded up with probability (discarded bits) / 2^16 for
+// r16 uniform in [0, 2^16): adding r16 below the kept 16 bits and truncating
+// (a carry into the exponent is the correct next value); non-finite values
+// convert as rounding to nearest does.
+__device__ __forceinline__ unsigned short bf16_bits_sr(float v, uint32_t r16) {
+    const uint32_t b = __float_as_uint(v);
+    if ((b & 0x7f800000u) == 0x7f800000u) return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+    return (unsigned short)((b + r16) >> 16);
+}
 
 // Storage forms: every form holds g_q = f_q - w_q rho0 (the offset from rest).
 // ld / st work on any address space (global, shared stage, local); ldg / stg
@@ -181,6 +235,8 @@ struct SweepArgs {
 // (evict-first) cache hint, ld.global.cs / st.global.cs (measured 4-5 %
 // faster sweeps on GB300).  A .global access on a shared or local address is
 // an invalid-address-space fault, so stage and register copies use ld / st.
+// stg(p, v, r16) is the sweep's store: r16 are the rounding bits of Rnd (used
+// by the BF16 form only).  bits(v, r16) gives the stored bit pattern.
 template <int PREC> struct Store;
 template <> struct Store<LBM_F64> {
     using T = double;
@@ -189,6 +245,7 @@ template <> struct Store<LBM_F64> {
     static __device__ __forceinline__ void st(T *p, C v) { *p = v; }
     static __device__ __forceinline__ C ldg(const T *p) { return __ldcs(p); }
     static __device__ __forceinline__ void stg(T *p, C v) { __stcs(p, v); }
+    static __device__ __forceinline__ void stg(T *p, C v, uint32_t) { __stcs(p, v); }
 };
 template <> struct Store<LBM_F32> {
     using T = float;
@@ -197,6 +254,7 @@ template <> struct Store<LBM_F32> {
     static __device__ __forceinline__ void st(T *p, C v) { *p = v; }
     static __device__ __forceinline__ C ldg(const T *p) { return __ldcs(p); }
     static __device__ __forceinline__ void stg(T *p, C v) { __stcs(p, v); }
+    static __device__ __forceinline__ void stg(T *p, C v, uint32_t) { __stcs(p, v); }
 };
 template <> struct Store<LBM_F16_OFFSET> {
     using T = __half;
@@ -205,6 +263,11 @@ template <> struct Store<LBM_F16_OFFSET> {
     static __device__ __forceinline__ void st(T *p, C v) { *p = __float2half_rn(v); }
     static __device__ __forceinline__ C ldg(const T *p) { return __half2float(__ldcs(p)); }
     static __device__ __forceinline__ void stg(T *p, C v) { __stcs(p, __float2half_rn(v)); }
+    static __device__ __forceinline__ void stg(T *p, C v, uint32_t) { __stcs(p, __float2half_rn(v)); }
+    static __device__ __forceinline__ unsigned short bits(C v, uint32_t) {
+        return __half_as_ushort(__float2half_rn(v));
+    }
+    static __device__ __forceinline__ C from_bits(unsigned short h) { return __half2float(__ushort_as_half(h)); }
 };
 template <> struct Store<LBM_BF16_OFFSET> {
     using T = __nv_bfloat16;
@@ -213,6 +276,13 @@ template <> struct Store<LBM_BF16_OFFSET> {
     static __device__ __forceinline__ void st(T *p, C v) { *p = __float2bfloat16_rn(v); }
     static __device__ __forceinline__ C ldg(const T *p) { return __bfloat162float(__ldcs(p)); }
     static __device__ __forceinline__ void stg(T *p, C v) { __stcs(p, __float2bfloat16_rn(v)); }
+    static __device__ __forceinline__ void stg(T *p, C v, uint32_t r16) {
+        __stcs(reinterpret_cast<unsigned short *>(p), bf16_bits_sr(v, r16));
+    }
+    static __device__ __forceinline__ unsigned short bits(C v, uint32_t r16) { return bf16_bits_sr(v, r16); }
+    static __device__ __forceinline__ C from_bits(unsigned short h) {
+        return __bfloat162float(__ushort_as_bfloat16(h));
+    }
 };
 
 
@@ -302,14 +372,23 @@ constexpr uint32_t ERR_TIMEOUT = 2u;
 constexpr uint32_t ERR_FSLIP_BODY = 4u;  // a body reached the fluid layer next to a free-slip wall
 
 // --- launchers (defined in the .cu files) ---------------------------------
-// Sweep variants: direct (one cell per thread, `block` threads per block),
-// staged (tiles of 256 cells brought into shared memory by bulk asynchronous
-// copies) and ring (per-thread asynchronous prefetch ring, block 256).
+// Sweep variants: direct (`cpt` consecutive cells per thread, `block`
+// threads per block, tiles of cpt * block cells), staged (tiles of 256 cells
+// brought into shared memory by bulk asynchronous copies) and ring
+// (per-thread asynchronous prefetch ring, block 256).
 constexpr int SWEEP_DIRECT = 0;
 constexpr int SWEEP_STAGED = 1;
 constexpr int SWEEP_RING = 2;
-cudaError_t launch_sweep(int prec, int parity, int variant, const SweepArgs &a, int grid, int block,
+cudaError_t launch_sweep(int prec, int parity, int variant, const SweepArgs &a, int grid, int block, int cpt,
                          cudaStream_t s);
+template <int PREC>
+cudaError_t launch_sweep_prec(int parity, int variant, const SweepArgs &a, int grid, int block, int cpt,
+                              cudaStream_t s);
+template <int PREC> int sweep_max_blocks_prec(int variant, int block, int cpt);
+// Cells per thread the direct sweep supports in storage form prec (1, 2, 4).
+inline bool sweep_cpt_supported(int prec, int cpt) {
+    return cpt == 1 || cpt == 2 || (cpt == 4 && prec != LBM_F64);
+}
 // Fill map[t] = lattice of tile t for the current tile size (lat: device table).
 cudaError_t launch_tile_map(const LatDev *lat, int nlat, int ntiles, int *map, cudaStream_t s);
 
@@ -340,7 +419,7 @@ cudaError_t launch_mlp_grad(const MlpArgs &m, cudaStream_t s);
 cudaError_t launch_adam(const MlpArgs &m, float lr, float beta1, float beta2, float eps, float c1, float c2,
                         cudaStream_t s);
 cudaError_t launch_to_half(const float *src, __half *dst, int n, cudaStream_t s);
-int sweep_max_active_blocks(int prec, int variant, int block);
+int sweep_max_active_blocks(int prec, int variant, int block, int cpt);
 constexpr int STAGED_TILE = 256;
 
 // Link word of a fluid cell (PartDev-independent, kept by the flags pass):
@@ -366,6 +445,7 @@ struct RemapArgs {
     int tile;            // cells per direct-sweep tile
     uint64_t *links;     // per-cell link words (LK_* layout)
     uint32_t *nbody;     // per-cell first neighbouring body
+    uint32_t *tick;      // step counter, advanced once per rigid-body update
 };
 // Recount every tile bit from the flags (bit t = tile t holds a nonzero flag).
 cudaError_t launch_tile_bits(const RemapArgs &a, int ntiles, cudaStream_t s);
@@ -377,6 +457,7 @@ cudaError_t launch_remap_step(int prec, int next_parity, const RemapArgs &a, int
 // state of the barrier, left at count 0 by every completed launch.
 struct GridBar {
     unsigned count, gen;
+    unsigned limit;  // polls before a wait gives up (0: the default, 2^20)
 };
 // Co-resident blocks of the fused kernel over the device (0: no cooperative launch).
 int remap_fused_max_blocks();

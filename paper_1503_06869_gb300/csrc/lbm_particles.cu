@@ -194,13 +194,20 @@ __device__ void rigid_unit(const RemapArgs &a, int warp, int lane) {
     if (warp >= P.np) {
         const int t = warp - P.np;
         if (t >= a.nlat) return;
+        // the step counter (seed of the next sweep's stochastic rounding)
+        if (t == 0 && lane == 0 && a.tick) *a.tick += 1u;
         double *w = a.wall_acc + 6 * ((size_t)t * ACC_COPIES + lane);
         double s[6];
         for (int k = 0; k < 6; ++k) s[k] = w[k];
         for (int k = 0; k < 6; ++k) w[k] = 0.0;
         for (int k = 0; k < 6; ++k) s[k] = warp_sum(s[k]);
-        if (lane == 0)
+        if (lane == 0) {
             for (int k = 0; k < 6; ++k) a.wall_last[6 * t + k] = s[k];
+            // a non-finite population next to a wall shows in its momentum
+            bool fin = true;
+            for (int k = 0; k < 6; ++k) fin = fin && isfinite(s[k]);
+            if (!fin) atomicOr(a.err, ERR_NONFINITE);
+        }
         return;
     }
     const size_t t = (size_t)warp;
@@ -664,7 +671,8 @@ __global__ void flags_region_kernel(RemapArgs a, int bpb) {
 // barrier; gen: barriers completed.  Thread 0 of each block reads gen before
 // it arrives (gen cannot move before every block has arrived); the last block
 // to arrive resets count and advances gen, the others poll gen, at most
-// 2^20 times.  Returns false after setting ERR_TIMEOUT when the poll ran out.
+// b->limit times (2^20 when 0).  Returns false after setting ERR_TIMEOUT when
+// the poll ran out.
 __device__ bool grid_barrier(GridBar *b, uint32_t *err) {
     __shared__ int ok;
     __syncthreads();
@@ -677,9 +685,10 @@ __device__ bool grid_barrier(GridBar *b, uint32_t *err) {
             __threadfence();
             atomicAdd(&b->gen, 1u);
         } else {
+            const unsigned lim = b->limit ? b->limit : (1u << 20);
             unsigned it = 0;
             while (*(volatile unsigned *)&b->gen == g) {
-                if (++it == (1u << 20)) {
+                if (++it >= lim) {
                     good = 0;
                     atomicOr(err, ERR_TIMEOUT);
                     break;

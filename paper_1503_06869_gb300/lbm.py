@@ -54,7 +54,8 @@ class lbm_info(C.Structure):
                 ("nlattices", C.c_int), ("nparticles", C.c_int), ("steps_done", C.c_longlong),
                 ("device_bytes", C.c_size_t), ("sweep_grid", C.c_int), ("sweep_block", C.c_int),
                 ("bytes_per_population", C.c_int), ("sweep_split", C.c_int),
-                ("remap_fused", C.c_int), ("remap_grid", C.c_int)]
+                ("remap_fused", C.c_int), ("remap_grid", C.c_int),
+                ("cells_per_thread", C.c_int), ("device", C.c_int)]
 
 
 # name -> (restype, argtypes) for every entry point of include/lbm.h
@@ -77,8 +78,10 @@ SIGNATURES = {
                                         C.c_void_p]),
     "lbm_get_info": (C.c_int, [C.c_void_p, C.POINTER(lbm_info)]),
     "lbm_set_launch": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "lbm_set_cells_per_thread": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_autotune": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "lbm_set_graphs": (C.c_int, [C.c_void_p, C.c_int]),
+    "lbm_set_wait_limit": (C.c_int, [C.c_void_p, C.c_uint]),
     "lbm_set_sweep_split": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_set_remap_fused": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_set_momentum_stabilisation": (C.c_int, [C.c_void_p, C.c_int]),
@@ -233,6 +236,10 @@ def lbm_set_launch(ctx, block: int, grid: int = 0):
     _check(load().lbm_set_launch(ctx, block, grid), ctx)
 
 
+def lbm_set_cells_per_thread(ctx, cpt: int):
+    _check(load().lbm_set_cells_per_thread(ctx, cpt), ctx)
+
+
 def lbm_autotune(ctx):
     b, g = C.c_int(0), C.c_int(0)
     _check(load().lbm_autotune(ctx, C.byref(b), C.byref(g)), ctx)
@@ -249,6 +256,10 @@ def lbm_set_remap_fused(ctx, enable: bool):
 
 def lbm_set_momentum_stabilisation(ctx, enable: bool):
     _check(load().lbm_set_momentum_stabilisation(ctx, 1 if enable else 0), ctx)
+
+
+def lbm_set_wait_limit(ctx, polls: int):
+    _check(load().lbm_set_wait_limit(ctx, int(polls)), ctx)
 
 
 def lbm_set_graphs(ctx, enable: bool):

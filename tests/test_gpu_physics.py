@@ -1,15 +1,14 @@
 """GPU checks on the 256x128x128 shear workload (spheroid a = 24, b = 3):
 
 * storage precision: FP32, FP16-offset and BF16-offset runs against the FP64
-  run after 2,000 steps (velocity relative L2 over fluid cells, force and
-  torque of the last step); the FP64 path is the one pinned to the CPU
-  oracle at 1e-12 by the parity tests;
+  oracle after 2,000 steps (velocity relative L2 over fluid cells, force and
+  torque of one step from the oracle's state);
 * Jeffery's orbit: the body axis of the spheroid rotates with the period
   T = 2 pi (r + 1/r) / gamma of a spheroid of aspect ratio r in simple shear
   (Jeffery 1922); the angle psi = atan2(r sin phi, cos phi) of the axis
   projected on the flow-gradient plane advances linearly in time, so T is
   fitted from a partial orbit.  Walls at 38 % of the body length from each
-  other and a finite Reynolds number shift T: the check is a band.
+  other and a finite Reynolds number shift T: the check is a band of 10 %.
 
 Both start from the Couette profile of the moving walls (equilibrium
 populations), so the shear is developed at the body from the first step.
@@ -67,34 +66,38 @@ def particles_from_records(recs, template):
     return out
 
 
-def test_storage_precision_against_fp64(lbm):
-    """Trajectory error (velocity field after 2,000 steps from the same start)
-    and per-step force/torque error (one step of each form from the same
-    FP64 state)."""
+def test_storage_precision_against_the_oracle(lbm):
+    """The precision study of the 256x128x128 workload: FP32, FP16-offset and
+    BF16-offset runs against the FP64 oracle (OpenMP over the host cores)
+    after 2,000 steps from the same Couette start -- velocity relative L2 over
+    fluid cells -- and the per-step force/torque error: one step of each form
+    from the oracle's state after 2,000 steps against the oracle's step."""
+    import os
+    import oracle
     w = large_shear(seed=1)
     lat = w.lattices[0]
     steps = 2000
-    runs = {}
-    for prec in ("f64", "f32", "f16", "bf16"):
+    o = oracle.Sim(lat, w.particles, openmp=True, threads=os.cpu_count() or 1)
+    o.set_pdfs(couette_pdfs(lat))
+    o.step(steps)
+    _, u0, fl0, _, pdfs0 = o.fields()
+    parts = particles_from_records(o.particles(), w.particles)
+    o.step(1)
+    F0, M0 = o.forces()
+    F0, M0 = F0[0], M0[0]
+    runs, loads = {}, {}
+    for prec in ("f32", "f16", "bf16"):
         s = start(lbm, w, prec)
         s.step(steps)
-        _, u, fl, _, pdfs = s.fields(0, pdfs=(prec == "f64"))
+        _, u, fl, _, _ = s.fields(0, pdfs=False)
         runs[prec] = (u, fl)
-        if prec == "f64":
-            state = (pdfs, s.particles())
         s.close()
-    # one step of every form from the FP64 state after 2,000 steps
-    parts = particles_from_records(state[1], w.particles)
-    loads = {}
-    for prec in ("f64", "f32", "f16", "bf16"):
         s = lbm.Simulation([lat], parts, prec=prec)
-        s.set_pdfs(state[0])
+        s.set_pdfs(pdfs0)
         s.step(1)
         F, M = s.forces()
         loads[prec] = (F[0], M[0])
         s.close()
-    u0, fl0 = runs["f64"]
-    F0, M0 = loads["f64"]
     # The body sits at the centre of a symmetric shear and rotates almost
     # freely: its net force is round-off and its torque nearly zero, so both
     # are measured against the hydrodynamic scales mu gamma a b and
@@ -103,9 +106,13 @@ def test_storage_precision_against_fp64(lbm):
     mu = lat.rho0 * (lat.tau - 0.5) / 3.0
     gamma = abs(lat.wall_u_hi[0] - lat.wall_u_lo[0]) / (lat.ny - 2.0)
     sF, sM = mu * gamma * a * b, mu * gamma * a * a * b
-    tol = {"f32": (1e-4, 1e-4), "f16": (2e-2, 5e-2), "bf16": (5e-2, 2e-1)}
+    # velocity: the stated 1e-2 of the reduced-precision storage forms; FP32
+    # (1e-5 in the short parity runs) accumulates round-off differences of
+    # the body's trajectory over 2,000 steps; forces and torques as the
+    # full-size parity test
+    tol = {"f32": (1e-4, 1e-4), "f16": (1e-2, 2e-2), "bf16": (1e-2, 5e-2)}
     report = {}
-    for prec, (eu_max, ef_max) in tol.items():
+    for prec in tol:
         u, fl = runs[prec]
         F, M = loads[prec]
         m = (fl0 == 0) & (fl == 0)
@@ -113,7 +120,7 @@ def test_storage_precision_against_fp64(lbm):
         eF = np.linalg.norm(F - F0) / sF
         eM = np.linalg.norm(M - M0) / sM
         report[prec] = (eu, eF, eM)
-    print("storage precision vs FP64: velocity rel L2 after 2000 steps, per-step |dF|/(mu g a b), "
+    print("storage precision vs the FP64 oracle: velocity rel L2 after 2000 steps, per-step |dF|/(mu g a b), "
           "|dM|/(mu g a^2 b):", {k: tuple(float(f"{x:.3e}") for x in v) for k, v in report.items()})
     for prec, (eu_max, ef_max) in tol.items():
         eu, eF, eM = report[prec]
@@ -149,4 +156,4 @@ def test_jeffery_period_from_a_partial_orbit(lbm):
     print(f"Jeffery period: fitted {T_fit:.0f} steps over {int(t[-1])} steps, "
           f"closed form {T_jeffery:.0f} (ratio {T_fit / T_jeffery:.3f})")
     assert slope < 0  # clockwise in the x-y plane for u_x = gamma y
-    assert 0.7 < T_fit / T_jeffery < 1.5
+    assert 0.9 < T_fit / T_jeffery < 1.1

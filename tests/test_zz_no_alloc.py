@@ -7,8 +7,10 @@ acceptable).  It writes into device buffers the caller already holds and
 keeps its per-block counts in a fixed device array.  This test calls it
 through the C interface twice in a row, with time steps in between so that
 the second call sees different links, and checks each result against the
-allocating lbm_get_links.  It also checks that a lattice above the fixed
-array's limit is refused.  Named to be collected last.
+allocating lbm_get_links, then calls it on a larger lattice followed by a
+smaller one (the smaller call must not see the counts the larger one left in
+the shared array).  It also checks that a lattice above the fixed array's
+limit is refused.  Named to be collected last.
 """
 import ctypes as C
 
@@ -65,6 +67,24 @@ def test_noalloc_links_match_allocating_call_twice(env):
     n, idx3, _, _ = _noalloc_links(torch, lib, sim.h, 10)
     assert n == len(idx) and np.array_equal(idx3, idx[:10])
     sim.close()
+
+
+def test_noalloc_links_larger_lattice_then_smaller(env):
+    torch, lbm, lib = env
+    rng = SplitMix64(12)
+    big = lbm.Simulation(shear_lattice(96, 64, 48, 0.8, 0.02),
+                         [Particle(pos=(47.1, 31.4, 23.9), quat=quat_from_axis(rng.unit_vector()),
+                                   semi_axes=(20.0, 4.0, 4.0), density=5.0)], prec="f32")
+    small = lbm.Simulation(shear_lattice(30, 18, 14, 0.8, 0.02),
+                           [Particle(pos=(14.2, 8.7, 6.6), quat=quat_from_axis(rng.unit_vector()),
+                                     semi_axes=(6.0, 2.5, 2.5), density=5.0)], prec="f32")
+    for sim in (big, small, big, small):
+        idx, q, pid = lbm.lbm_get_links(sim.h)
+        n, idx2, q2, pid2 = _noalloc_links(torch, lib, sim.h, len(idx) + 8)
+        assert n == len(idx)
+        assert np.array_equal(idx2, idx) and np.array_equal(q2, q) and np.array_equal(pid2, pid)
+    big.close()
+    small.close()
 
 
 def test_noalloc_links_refuse_lattices_above_the_limit(env):
