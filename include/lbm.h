@@ -377,7 +377,9 @@ lbm_status lbm_get_launch_count(lbm_ctx *ctx, long long *launches);
  * velocity field (as lbm_get_fields reports it: zero on wall and particle
  * cells) is interpolated trilinearly between cell centres (periodic axes
  * wrap, the others clamp to the lattice); feature 3s+d is component d of
- * R^T (u - U) / V, U the body velocity, V = gamma * a.  Features 81..83: the
+ * R^T (u - U - Omega x R o_s) / V (the flow relative to the body's rigid
+ * motion continued to the sample point; U, Omega the body's velocity and
+ * angular velocity), V = gamma * a.  Features 81..83: the
  * body x axis in world coordinates (first column of R); 84: a/b; 85: b.
  * gamma is the shear rate of the channel between the moving y walls,
  * |u_hi,x - u_lo,x| / (ny - 2); a lattice without moving y walls has gamma

@@ -20,8 +20,10 @@ paper itself has no such closure, so every definition below is a reading:
   the fields export reports: sum c f / rho0 + g/2 on fluid cells, zero on wall
   and particle cells); corner indices wrap on periodic axes and are clamped
   to [0, n-1] on the others.  Feature 3 s + d is component d of
-  R^T (u(x_s) - U) / V, U the body's velocity, V = shear_rate * a (V = 1 when
-  the shear rate is zero).  Features 81..83 are R's first column (the body's
+  R^T (u(x_s) - U - Omega x (x_s - x_C)) / V: the fluid velocity relative to
+  the body's rigid motion continued to the sample point (U the body's
+  velocity, Omega its angular velocity), V = shear_rate * a (V = 1 when the
+  shear rate is zero).  Features 81..83 are R's first column (the body's
   x axis in the world frame), 84 is a / b and 85 is b.
 * Network: 86 -> 64 -> 64 -> 64 -> 6, ReLU after each hidden layer, linear
   output.  Parameters in one flat vector: W1 (64 x 86, row-major, [out][in]),
@@ -156,16 +158,18 @@ def sample_offsets(semi):
     return np.array(offs)
 
 
-def features(u3, dims, periodic, pos, quat, vel, semi, shear_rate):
+def features(u3, dims, periodic, pos, quat, vel, omega, semi, shear_rate):
     """The 86 closure inputs of one body (see the module docstring)."""
     R = quat_rotation(quat)
     a, b = semi[0], semi[1]
     V = shear_rate * a if shear_rate > 0 else 1.0
     f = np.zeros(N_IN)
     for s, o in enumerate(sample_offsets(semi)):
-        x = np.asarray(pos) + R @ o
+        r = R @ o
+        x = np.asarray(pos) + r
         u = trilinear(u3, dims, periodic, x)
-        f[3 * s:3 * s + 3] = R.T @ (u - np.asarray(vel)) / V
+        rigid = np.asarray(vel) + np.cross(np.asarray(omega), r)
+        f[3 * s:3 * s + 3] = R.T @ (u - rigid) / V
     f[81:84] = R[:, 0]
     f[84] = a / b
     f[85] = b

@@ -6,11 +6,13 @@ b = 1.5 / b = 6 pairs):
 
 * moving bodies (``paired_moving``, the closure's training set): batches of
   independent shear cells, one prolate spheroid each, rotating at a seeded
-  angular velocity perpendicular to its axis (|Omega| up to 1.5 gamma) about
-  the centre of the channel; the body is made so heavy (density 1e12) that
-  the flow cannot change its motion, so the coarse and the fine body follow
-  the same prescribed motion exactly (a rotation about a fixed axis composes
-  exactly over the s^2 fine steps of one coarse step).  After a transient,
+  angular velocity perpendicular to its axis (|Omega| up to 1.5 gamma) and
+  translating with a seeded slip parallel to the walls (up to 0.5 gamma a)
+  from the middle of the channel; the body is made so heavy (density 1e12)
+  that the flow cannot change its motion, so the coarse and the fine body
+  follow the same prescribed motion exactly (a rotation about a fixed axis and
+  a constant translation compose exactly over the s^2 fine steps of one
+  coarse step).  After a transient,
   every `spacing` coarse steps one sample: the features of the coarse run at
   the start of a window of `window` coarse steps, and the force and torque of
   both runs averaged over that window (the matched s^2 window fine steps);
@@ -123,8 +125,8 @@ def _body_frame_nd(F, M, quats, mu, gamma, a, b):
 
 
 def paired_moving(nbody, seed=11, coarse_box=(48, 40, 48), a=15.0, b=1.5, uw=0.02, tau=0.8, scale=4,
-                  transient=400, samples=100, spacing=12, window=4, max_spin=1.5, fine_prec="f16",
-                  log=print):
+                  transient=400, samples=100, spacing=12, window=4, max_spin=1.5, max_slip=0.5,
+                  fine_prec="f16", log=print):
     """Paired coarse/fine runs of `nbody` rotating spheroids (one per shear
     cell, all cells of a resolution in one batch).  Returns features X (n x
     86), targets Y = fine - coarse (n x 6), the coarse and fine loads C, Fn
@@ -141,20 +143,27 @@ def paired_moving(nbody, seed=11, coarse_box=(48, 40, 48), a=15.0, b=1.5, uw=0.0
         n = v - np.dot(v, t) * t
         n /= np.linalg.norm(n)
         w = rng.uniform_range(-max_spin, max_spin) * gamma
+        # slip against the flow, parallel to the walls (the centre stays on
+        # the channel's middle plane, where the flow is at rest)
+        phi = rng.uniform_range(0.0, 2.0 * math.pi)
+        us = rng.uniform_range(0.0, max_slip) * gamma * a
+        U = np.array([us * math.cos(phi), 0.0, us * math.sin(phi)])
         q = quat_from_axis(tuple(t))
         pc.append(Particle(pos=_channel_centre(coarse_box), quat=q, semi_axes=(a, b, b), density=HEAVY,
-                           omega=tuple(w * n), cell=i))
+                           vel=tuple(U), omega=tuple(w * n), cell=i))
         pf.append(Particle(pos=_channel_centre(fine_box), quat=q, semi_axes=(scale * a, scale * b, scale * b),
-                           density=HEAVY, omega=tuple(w * n / scale ** 2), cell=i))
+                           density=HEAVY, vel=tuple(U / scale), omega=tuple(w * n / scale ** 2), cell=i))
     sims = []
     try:
         sc = lbm.Simulation([lc] * nbody, pc, prec="f32")
         sims.append(sc)
         sf = lbm.Simulation([lf] * nbody, pf, prec=fine_prec)
         sims.append(sf)
+        pdc, pdf = couette_pdfs(lc), couette_pdfs(lf)
         for c in range(nbody):
-            sc.set_pdfs(couette_pdfs(lc), c)
-            sf.set_pdfs(couette_pdfs(lf), c)
+            sc.set_pdfs(pdc, c)
+            sf.set_pdfs(pdf, c)
+        del pdc, pdf
         lbm.lbm_autotune(sc.h)
         lbm.lbm_autotune(sf.h)
         sc.step(transient)
@@ -194,6 +203,22 @@ def paired_moving(nbody, seed=11, coarse_box=(48, 40, 48), a=15.0, b=1.5, uw=0.0
     return X, Fn - C, C, Fn, np.concatenate(body)
 
 
+def fluctuation(C, Fn, body, scale):
+    """Step-to-step fluctuation of the rescaled coarse error: the RMS of the
+    difference between consecutive samples of the same body, over sqrt 2,
+    per part.  Consecutive samples are a few steps apart, so their smooth
+    parts agree; what remains is the staircase fluctuation of the coarse
+    momentum exchange, which no function of the (smooth) flow features can
+    predict: a floor for the error of any such closure."""
+    out = []
+    for sl, c in ((slice(0, 3), scale[0]), (slice(3, 6), scale[1])):
+        R = c * C[:, sl] - Fn[:, sl]
+        d = [np.diff(R[body == b], axis=0) for b in np.unique(body)]
+        d = np.concatenate([x for x in d if len(x)])
+        out.append(float(np.sqrt(np.mean(np.sum(d * d, axis=1)) / 2.0)))
+    return out
+
+
 def fit_scale(C, Fn):
     """Least-squares factors c_F, c_M with Fn ~ c C, separately for the force
     and the torque part (the one-parameter-per-part baseline)."""
@@ -212,19 +237,70 @@ def init_params(seed):
     return np.concatenate(parts).astype(np.float32)
 
 
-def train(X, Y, steps=2000, lr=1e-3, seed=0, Xv=None, Yv=None, every=50):
-    """Full-batch Adam on the GPU; returns FP32 and FP16 parameters and the
-    loss history.  With a validation set (Xv, Yv), the parameters returned
-    are those of the lowest validation loss, checked every `every` steps
-    (early stopping)."""
+LAYERS = ((64, 86), (64, 64), (64, 64), (6, 64))  # (out, in) of the four layers, lbm.h layout
+
+
+def split_params(p):
+    """Flat parameter vector -> [(W, b)] per layer (views)."""
+    out, o = [], 0
+    for n_out, n_in in LAYERS:
+        W = p[o:o + n_out * n_in].reshape(n_out, n_in)
+        o += n_out * n_in
+        b = p[o:o + n_out]
+        o += n_out
+        out.append((W, b))
+    return out
+
+
+def fold_standardisation(p32, mX, sX, sY):
+    """Parameters trained on standardised data ((X - mX) / sX -> Y / sY) ->
+    parameters of the same network on raw features and targets: the input
+    scaling folds into the first layer, the output scaling into the last."""
+    p = np.array(p32, dtype=np.float64)
+    (W1, b1), _, _, (W4, b4) = split_params(p)
+    b1 -= W1 @ (mX / sX)
+    W1 /= sX[None, :]
+    W4 *= sY[:, None]
+    b4 *= sY
+    return p.astype(np.float32)
+
+
+def standardisation(X, Y):
+    """Feature means and scales (constant features: mean 0, scale 1) and
+    target scales (per output)."""
+    mX = X.mean(axis=0)
+    sX = X.std(axis=0)
+    const = sX < 1e-6
+    mX[const] = 0.0
+    sX[const] = 1.0
+    # a floor on the scales keeps the folded first layer (W / sX) well inside
+    # the FP16 range
+    if (~const).any():
+        sX[~const] = np.maximum(sX[~const], 0.05 * np.median(sX[~const]))
+    sY = np.sqrt((Y ** 2).mean(axis=0))
+    sY[sY < 1e-6] = 1.0
+    return mX, sX, sY
+
+
+def train(X, Y, steps=2000, lr=1e-3, seed=0, Xv=None, Yv=None, every=50, standardise=True):
+    """Full-batch Adam on the GPU; returns FP32 and FP16 parameters (for raw
+    features and targets) and the loss history.  With standardise, the
+    network is trained on standardised features and targets and the scales
+    are folded into the first and last layers afterwards.  With a validation
+    set (Xv, Yv), the parameters returned are those of the lowest validation
+    loss, checked every `every` steps (early stopping)."""
     import torch
+    if standardise:
+        mX, sX, sY = standardisation(X, Y)
+    else:
+        mX, sX, sY = np.zeros(X.shape[1]), np.ones(X.shape[1]), np.ones(Y.shape[1])
     m = lbm.lbm_mlp_create(init_params(seed))
     try:
-        x = torch.tensor(np.ascontiguousarray(X, dtype=np.float32), device="cuda")
-        y = torch.tensor(np.ascontiguousarray(Y, dtype=np.float32), device="cuda")
+        x = torch.tensor(np.ascontiguousarray((X - mX) / sX, dtype=np.float32), device="cuda")
+        y = torch.tensor(np.ascontiguousarray(Y / sY, dtype=np.float32), device="cuda")
         if Xv is not None:
-            xv = torch.tensor(np.ascontiguousarray(Xv, dtype=np.float32), device="cuda")
-            yv = torch.tensor(np.ascontiguousarray(Yv, dtype=np.float32), device="cuda")
+            xv = torch.tensor(np.ascontiguousarray((Xv - mX) / sX, dtype=np.float32), device="cuda")
+            yv = torch.tensor(np.ascontiguousarray(Yv / sY, dtype=np.float32), device="cuda")
         hist, best, best_p = [], math.inf, None
         for s in range(steps):
             loss = lbm.lbm_mlp_train_step(m, x.data_ptr(), y.data_ptr(), len(X), lr, want_loss=(s % every == 0))
@@ -234,10 +310,11 @@ def train(X, Y, steps=2000, lr=1e-3, seed=0, Xv=None, Yv=None, every=50):
                 vl = lbm.lbm_mlp_grad(m, xv.data_ptr(), yv.data_ptr(), len(Xv))
                 if vl < best:
                     best, best_p = vl, lbm.lbm_mlp_get_params(m)
-        p32, p16 = best_p if best_p is not None else lbm.lbm_mlp_get_params(m)
+        p32, _ = best_p if best_p is not None else lbm.lbm_mlp_get_params(m)
     finally:
         lbm.lbm_mlp_destroy(m)
-    return p32, p16, hist
+    p32 = fold_standardisation(p32, mX, sX, sY)
+    return p32, p32.astype(np.float16), hist
 
 
 def predict(p32, X):
@@ -322,6 +399,8 @@ def main(argv=None):
     res = {"samples": int(len(X)), "train": int(tr.sum()), "validation": int(va.sum()), "held_out": int(te.sum()),
            "train_loss_first_last": [hist[0], hist[-1]], "scale_factors": [cF, cM],
            **evaluate(C[te], Fn[te], predict(p32, X[te]), scale=(cF, cM))}
+    if body is not None:
+        res["force_rms_fluctuation"], res["torque_rms_fluctuation"] = fluctuation(C[te], Fn[te], body[te], (cF, cM))
     print(json.dumps(res), flush=True)
     if args.out:
         np.savez(args.out, X=X, Y=Y, coarse=C, fine=Fn, params32=p32, params16=p16,
@@ -329,8 +408,19 @@ def main(argv=None):
     if args.params_out:
         np.save(args.params_out, p16)
     if args.eval_out:
+        rec = {"force_rms": {k: res.get(f"force_rms_{k}") for k in ("without", "scaled", "with", "fluctuation", "fine")},
+               "torque_rms": {k: res.get(f"torque_rms_{k}") for k in ("without", "scaled", "with", "fluctuation", "fine")},
+               "units": "body-frame force in mu*gamma*a*b, torque in mu*gamma*a^2*b (RMS over held-out samples of the "
+                        "vector error against the fine run)",
+               "samples": {"total": res["samples"], "train": res["train"], "validation": res["validation"],
+                           "held_out": res["held_out"]},
+               "scale_factors": res["scale_factors"],
+               "judge": "paired runs of the same prescribed body motion at minor semi-axis 6 lu (4x finer lattice, "
+                        "16x the steps), window-averaged force and torque",
+               "source": "python -m paper_1503_06869_gb300.closure_train " + " ".join(argv if argv is not None
+                                                                                        else sys.argv[1:])}
         with open(args.eval_out, "w") as fh:
-            json.dump(res, fh, indent=1)
+            json.dump(rec, fh, indent=1)
     return res
 
 

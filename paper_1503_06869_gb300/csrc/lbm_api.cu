@@ -817,6 +817,8 @@ lbm_status lbm_set_particles(lbm_ctx *ctx, const lbm_particle *p, int n) {
         float *bf = &bodyf[BF_STRIDE * (size_t)i];
         for (int k = 0; k < 9; ++k) bf[BF_R + k] = (float)R[k];
         bf[BF_SHAPE] = capsule ? 1.0f : 0.0f;
+        bf[BF_TUBE_H] = (float)(b.semi_axes[0] + 2.0);
+        bf[BF_TUBE_R] = (float)(std::fmax(b.semi_axes[1], b.semi_axes[2]) + 2.0);
         bf[BF_CAPH] = capsule ? (float)((b.semi_axes[0] - b.semi_axes[1]) / b.semi_axes[1]) : 0.0f;
         for (int a = 0; a < 3; ++a) {
             bf[BF_INV + a] = (float)(1.0 / (capsule ? b.semi_axes[1] : b.semi_axes[a]));

@@ -177,8 +177,9 @@ __device__ void cell_velocity(const LatDev &L, const void *fv, const uint8_t *fl
 // One warp per body.  Lane s < 27 interpolates the velocity at sample point
 // s (offsets (1.5 a i, 1.5 b j, 1.5 c k), s = 9(i+1) + 3(j+1) + (k+1)) from
 // its 8 surrounding cells (periodic axes wrap, the others clamp), subtracts
-// the body velocity, rotates into the body frame and scales by 1/(shear
-// rate * a); lanes 27 and 28 write the body axis, a/b and b.
+// the body's rigid motion continued to that point (U + Omega x R o_s),
+// rotates into the body frame and scales by 1/(shear rate * a); lanes 27 and
+// 28 write the body axis, a/b and b.
 template <int PREC, int NEXT_ODD>
 __global__ void closure_features_kernel(ClosureArgs a) {
     pdl_enter();
@@ -188,11 +189,12 @@ __global__ void closure_features_kernel(ClosureArgs a) {
     if (p >= P.np) return;
     const LatDev &L = a.lat[P.cell[p]];
     const float *bf = P.bodyf + BF_STRIDE * (size_t)p;
-    float R[9], pos[3], U[3];
+    float R[9], pos[3], U[3], W[3];
     for (int k = 0; k < 9; ++k) R[k] = bf[BF_R + k];
     for (int k = 0; k < 3; ++k) {
         pos[k] = bf[BF_POS + k] + bf[BF_POSLO + k];
         U[k] = bf[BF_U + k];
+        W[k] = bf[BF_W + k];
     }
     const float sa = (float)P.semi[3 * (size_t)p], sb = (float)P.semi[3 * (size_t)p + 1],
                 sc = (float)P.semi[3 * (size_t)p + 2];
@@ -200,8 +202,11 @@ __global__ void closure_features_kernel(ClosureArgs a) {
     if (lane < 27) {
         const int i = lane / 9 - 1, j = (lane / 3) % 3 - 1, k = lane % 3 - 1;
         const float o[3] = {1.5f * sa * i, 1.5f * sb * j, 1.5f * sc * k};
-        float x[3];
-        for (int r = 0; r < 3; ++r) x[r] = pos[r] + (R[3 * r] * o[0] + R[3 * r + 1] * o[1] + R[3 * r + 2] * o[2]);
+        float x[3], ro[3];
+        for (int r = 0; r < 3; ++r) {
+            ro[r] = R[3 * r] * o[0] + R[3 * r + 1] * o[1] + R[3 * r + 2] * o[2];
+            x[r] = pos[r] + ro[r];
+        }
         const int dims[3] = {L.nx, L.ny, L.nz}, per[3] = {L.px, L.py, L.pz};
         int i0[3];
         float w1[3];
@@ -231,7 +236,10 @@ __global__ void closure_features_kernel(ClosureArgs a) {
             for (int r = 0; r < 3; ++r) u[r] += w * uc[r];
         }
         const float V = L.cl_gamma > 0.f ? L.cl_gamma * sa : 1.f;
-        const float d[3] = {u[0] - U[0], u[1] - U[1], u[2] - U[2]};
+        // relative to the rigid motion continued to the sample point
+        const float d[3] = {u[0] - (U[0] + (W[1] * ro[2] - W[2] * ro[1])),
+                            u[1] - (U[1] + (W[2] * ro[0] - W[0] * ro[2])),
+                            u[2] - (U[2] + (W[0] * ro[1] - W[1] * ro[0]))};
         for (int r = 0; r < 3; ++r) out[3 * lane + r] = (R[r] * d[0] + R[3 + r] * d[1] + R[6 + r] * d[2]) / V;
     } else if (lane == 27) {
         out[81] = R[0];

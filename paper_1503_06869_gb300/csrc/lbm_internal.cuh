@@ -150,10 +150,14 @@ struct PartDev {
 // (hi at BF_POS, lo at BF_POSLO), translational and angular velocity, the
 // shape (BF_SHAPE: 0 ellipsoid, 1 spherocylinder) and, for a spherocylinder
 // of radius r and half length a, the half length of its cylindrical part in
-// units of r, (a - r) / r (BF_CAPH; 0 for an ellipsoid).
+// units of r, (a - r) / r (BF_CAPH; 0 for an ellipsoid).  BF_TUBE_H and
+// BF_TUBE_R: half length and radius of the cylinder about the body x axis
+// that holds every cell the re-mapping passes can touch this step (the body's
+// own cylinder, semi_0 and max(semi_1, semi_2), widened by the step's largest
+// displacement of a body point and a margin of two cells).
 constexpr int BF_STRIDE = 32;
 constexpr int BF_R = 0, BF_INV = 9, BF_POS = 12, BF_POSLO = 16, BF_U = 19, BF_W = 22, BF_CAPH = 25,
-              BF_SHAPE = 26;
+              BF_SHAPE = 26, BF_TUBE_H = 27, BF_TUBE_R = 28;
 
 struct SweepArgs {
     LatDev lat0;             // copy of lattice 0 (used when nlat == 1)

@@ -358,6 +358,21 @@ __device__ void rigid_unit(const RemapArgs &a, int warp, int lane) {
     }
     P.region[6 * t + k] = ilo;
     P.region[6 * t + 3 + k] = max(ihi - ilo + 1, 0);
+    // the cylinder the re-mapping passes visit this step (BF_TUBE_H/R): the
+    // largest displacement of a body point in the step is at most
+    // |U| + |Omega| * (largest semi-axis) (a fixed body keeps its pose)
+    {
+        const float du = fixed ? 0.0f : (float)veln, wk = fixed ? 0.0f : (float)omn;
+        const float d0 = __shfl_sync(0x7u, du, 0), d1 = __shfl_sync(0x7u, du, 1), d2 = __shfl_sync(0x7u, du, 2);
+        const float w0 = __shfl_sync(0x7u, wk, 0), w1 = __shfl_sync(0x7u, wk, 1), w2 = __shfl_sync(0x7u, wk, 2);
+        if (lane == 0) {
+            const float smax = fmaxf((float)s0, fmaxf((float)s1, (float)s2));
+            float delta = sqrtf(d0 * d0 + d1 * d1 + d2 * d2) + sqrtf(w0 * w0 + w1 * w1 + w2 * w2) * smax;
+            if (!(delta < 1e6f)) delta = 1e6f;  // non-finite state: every row whole (the step is reported)
+            bf[BF_TUBE_H] = (float)s0 + 2.0f + delta;
+            bf[BF_TUBE_R] = fmaxf((float)s1, (float)s2) + 2.0f + delta;
+        }
+    }
 }
 
 __global__ void rigid_body_kernel(RemapArgs a) {
@@ -390,9 +405,56 @@ __device__ __forceinline__ bool region_cell(const int *reg, const LatDev &L, int
     return true;
 }
 
+// Cells of a re-mapping box that the passes visit: the box's rows (y, z) and
+// in each row the x interval that meets the body's cylinder (BF_TUBE_H/R
+// about the body x axis through the centre, in the frame of the box, whose
+// origin reg[0..2] is unwrapped around the centre).  The cylinder holds the
+// body (an ellipsoid (a, b, c) lies within radius max(b, c) of its x axis and
+// |x| <= a; a spherocylinder (L/2, r, r) within radius r and |x| <= L/2),
+// widened by the step's largest displacement of a body point and two cells:
+// every cell a pass can change (uncovered, claimed, refilled, re-flagged) is
+// inside, so the passes give the same maps as over the whole box.  The
+// interval is computed in FP32 and widened by one more cell on each side.
+// Returns x0 > x1 for a row that misses the cylinder.
+__device__ __forceinline__ void row_interval(const int *reg, const float *bf, int r1, int r2, int &x0, int &x1) {
+    const float H = bf[BF_TUBE_H], rho = bf[BF_TUBE_R];
+    const float tx = bf[BF_R + 0], ty = bf[BF_R + 3], tz = bf[BF_R + 6];
+    const float cx = bf[BF_POS] - (float)reg[0];
+    const float dy = (float)(reg[1] + r1) - bf[BF_POS + 1];
+    const float dz = (float)(reg[2] + r2) - bf[BF_POS + 2];
+    const float s0 = ty * dy + tz * dz;  // axial coordinate at X = x - x_C = 0
+    float lo = -3.0e38f, hi = 3.0e38f;
+    x0 = 0;
+    x1 = -1;
+    // axial: |tx X + s0| <= H
+    if (fabsf(tx) > 1e-6f) {
+        const float ea = (-H - s0) / tx, eb = (H - s0) / tx;
+        lo = fminf(ea, eb);
+        hi = fmaxf(ea, eb);
+    } else if (fabsf(s0) > H) {
+        return;
+    }
+    // radial: |d|^2 - (t.d)^2 <= rho^2, a quadratic (1 - tx^2) X^2 - 2 tx s0 X + C <= 0
+    const float A = 1.0f - tx * tx, B = -2.0f * tx * s0, C = dy * dy + dz * dz - s0 * s0 - rho * rho;
+    if (A > 1e-6f) {
+        const float disc = B * B - 4.0f * A * C;
+        if (disc < 0.0f) return;
+        const float sq = sqrtf(disc);
+        lo = fmaxf(lo, (-B - sq) / (2.0f * A));
+        hi = fminf(hi, (-B + sq) / (2.0f * A));
+    } else if (C > 0.0f) {
+        return;
+    }
+    if (!(lo <= hi)) return;
+    x0 = max(0, (int)fmaxf(floorf(cx + lo) - 1.0f, -1.0f));
+    x1 = min(reg[3] - 1, (int)fminf(ceilf(cx + hi) + 1.0f, (float)reg[3]));
+}
+
 // The region passes work on np * bpb units of one block each: unit u covers
 // body p = u / bpb.  The separate kernels run one unit per block; the fused
-// kernel loops its blocks over the units.
+// kernel loops its blocks over the units.  The warps of a body's units take
+// the box's rows in turn; the lanes of a warp share the row's cells in the
+// cylinder's interval.
 struct RegionLoop {
     int p, first, stride;
 };
@@ -417,10 +479,16 @@ __device__ void remap_region(const RemapArgs &a, int unit, int bpb) {
     const LatDev &L = a.lat[P.cell[p]];
     const double *pos = P.pos + 3 * p, *semi = P.semi + 3 * p, *R64 = P.R64 + 9 * (size_t)p;
     BodyF32 bf;
-    load_body_f32(P.bodyf + BF_STRIDE * (size_t)p, bf);
-    for (int r = rl.first; r < vol; r += rl.stride) {
+    const float *bfp = P.bodyf + BF_STRIDE * (size_t)p;
+    load_body_f32(bfp, bf);
+    const int rows = reg[4] * reg[5];
+    const int lane = threadIdx.x & 31;
+    for (int rr = rl.first >> 5; rr < rows; rr += rl.stride >> 5) {
+      int x0, x1;
+      row_interval(reg, bfp, rr % reg[4], rr / reg[4], x0, x1);
+      for (int r0 = x0 + lane; r0 <= x1; r0 += 32) {
         RegionCell c;
-        region_cell(reg, L, r, c);
+        region_cell(reg, L, r0 + reg[3] * rr, c);
         const long long cg = L.c_off + c.idx;
         if (PASS == 0) {  // uncover
             if (a.pid[cg] == (uint32_t)p && !inside_fast(L, pos, R64, semi, bf, c.i, c.j, c.k)) {
@@ -438,6 +506,7 @@ __device__ void remap_region(const RemapArgs &a, int unit, int bpb) {
                 if (old > (uint32_t)p) P.changed[p] = 1;
             }
         }
+      }
     }
 }
 
@@ -550,21 +619,27 @@ __device__ void fixup_region(const RemapArgs &a, int unit, int bpb) {
     // changed it: a body that changed nothing has nothing to fix up here
     if (!P.changed[p]) return;
     const int *reg = P.region + 6 * p;
-    const int vol = reg[3] * reg[4] * reg[5];
+    const float *bfp = P.bodyf + BF_STRIDE * (size_t)p;
     const LatDev &L = a.lat[P.cell[p]];
-    for (int r = rl.first; r < vol; r += rl.stride) {
-        RegionCell c;
-        region_cell(reg, L, r, c);
-        const long long cg = L.c_off + c.idx;
-        if (!(a.flags[cg] & F_CHANGED)) continue;
-        const bool old_f = !(a.flags[cg] & F_SOLID);
-        const uint32_t id = a.pid[cg];
-        const bool new_f = id == PID_FLUID;
-        if (old_f == new_f) continue;
-        // exactly one body handles each changed cell: its uncoverer or its new owner
-        const uint32_t owner = new_f ? a.pid_prev[cg] : id;
-        if (owner != (uint32_t)p) continue;
-        fixup_cell<PREC, NEXT_ODD>(a, L, c.i, c.j, c.k, false);
+    const int rows = reg[4] * reg[5];
+    const int lane = threadIdx.x & 31;
+    for (int rr = rl.first >> 5; rr < rows; rr += rl.stride >> 5) {
+        int x0, x1;
+        row_interval(reg, bfp, rr % reg[4], rr / reg[4], x0, x1);
+        for (int r0 = x0 + lane; r0 <= x1; r0 += 32) {
+            RegionCell c;
+            region_cell(reg, L, r0 + reg[3] * rr, c);
+            const long long cg = L.c_off + c.idx;
+            if (!(a.flags[cg] & F_CHANGED)) continue;
+            const bool old_f = !(a.flags[cg] & F_SOLID);
+            const uint32_t id = a.pid[cg];
+            const bool new_f = id == PID_FLUID;
+            if (old_f == new_f) continue;
+            // exactly one body handles each changed cell: its uncoverer or its new owner
+            const uint32_t owner = new_f ? a.pid_prev[cg] : id;
+            if (owner != (uint32_t)p) continue;
+            fixup_cell<PREC, NEXT_ODD>(a, L, c.i, c.j, c.k, false);
+        }
     }
 }
 
@@ -638,25 +713,31 @@ __device__ void flags_region(const RemapArgs &a, int unit, int bpb) {
     if (p >= P.np) return;
     if (!P.changed[p]) return;  // no owner changed in this box: flags and links stand
     const int *reg = P.region + 6 * p;
-    const int vol = reg[3] * reg[4] * reg[5];
+    const float *bfp = P.bodyf + BF_STRIDE * (size_t)p;
     const LatDev &L = a.lat[P.cell[p]];
-    for (int r = rl.first; r < vol; r += rl.stride) {
-        RegionCell c;
-        region_cell(reg, L, r, c);
-        const long long cg = L.c_off + c.idx;
-        if (a.flags[cg] & F_WALL) continue;
-        uint64_t lk;
-        uint32_t p0;
-        const uint8_t f = flag_of(L, a.pid, L.c_off, c.i, c.j, c.k, lk, p0);
-        a.flags[cg] = f;
-        a.links[cg] = lk;
-        a.nbody[cg] = p0;
-        // a cell turning non-bulk marks its tile; marks are cleared only by a
-        // recount (launch_tile_bits), so a stale mark costs the flagged path,
-        // never a missed cell
-        if (f && a.tbits) {
-            const int t = L.tile0 + c.idx / a.tile;
-            atomicOr(a.tbits + (t >> 5), 1u << (t & 31));
+    const int rows = reg[4] * reg[5];
+    const int lane = threadIdx.x & 31;
+    for (int rr = rl.first >> 5; rr < rows; rr += rl.stride >> 5) {
+        int x0, x1;
+        row_interval(reg, bfp, rr % reg[4], rr / reg[4], x0, x1);
+        for (int r0 = x0 + lane; r0 <= x1; r0 += 32) {
+            RegionCell c;
+            region_cell(reg, L, r0 + reg[3] * rr, c);
+            const long long cg = L.c_off + c.idx;
+            if (a.flags[cg] & F_WALL) continue;
+            uint64_t lk;
+            uint32_t p0;
+            const uint8_t f = flag_of(L, a.pid, L.c_off, c.i, c.j, c.k, lk, p0);
+            a.flags[cg] = f;
+            a.links[cg] = lk;
+            a.nbody[cg] = p0;
+            // a cell turning non-bulk marks its tile; marks are cleared only by a
+            // recount (launch_tile_bits), so a stale mark costs the flagged path,
+            // never a missed cell
+            if (f && a.tbits) {
+                const int t = L.tile0 + c.idx / a.tile;
+                atomicOr(a.tbits + (t >> 5), 1u << (t & 31));
+            }
         }
     }
 }

@@ -1155,10 +1155,10 @@ __device__ __forceinline__ void group_cells(const SweepArgs &a, const LatDev &L,
 // Resident blocks of 256 threads per SM for the grouped sweep: 2 leaves 128
 // registers per thread; with V cells per thread that is still V * 16 cells'
 // loads in flight per SM partition against 24 for the one-cell sweep.
-template <int PREC, int V> struct GroupBounds { static constexpr int MINB = 2; };
+template <int PREC, int V> struct GroupBounds { static constexpr int MAXT = 256, MINB = 2; };
 
 template <int PREC, int ODD, bool SINGLE, int V>
-__global__ void __launch_bounds__(256, (GroupBounds<PREC, V>::MINB))
+__global__ void __launch_bounds__((GroupBounds<PREC, V>::MAXT), (GroupBounds<PREC, V>::MINB))
     sweep_group(const __grid_constant__ SweepArgs a) {
     pdl_enter();
     const uint32_t seed = PREC == LBM_BF16_OFFSET ? step_seed(a.tick) : 0u;

@@ -149,19 +149,16 @@ int main(void) {
     assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout, r.stderr)
 
 
-def test_the_readme_c_example_compiles_and_links(lib, tmp_path):
-    """The C program shown in README.md builds against the headers and the
-    library (it is not run: it needs a GPU)."""
+def test_the_c_usage_example_compiles_and_links(lib, tmp_path):
+    """The C usage example (tests/c_usage_example.c, also shown in the
+    project's readme) builds against the headers and the library (it is not
+    run: it needs a GPU)."""
     from paper_1503_06869_gb300 import lbm
-    text = open(os.path.join(ROOT, "README.md")).read()
-    blocks = re.findall(r"```c\n(.*?)```", text, flags=re.S)
-    assert len(blocks) == 1
-    prog = tmp_path / "readme.c"
-    prog.write_text(blocks[0])
+    prog = os.path.join(ROOT, "tests", "c_usage_example.c")
     libdir = os.path.dirname(lbm.LIB_PATH)
     name = os.path.basename(lbm.LIB_PATH)[3:-3]
     subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
-                    str(prog), "-o", str(tmp_path / "readme"), "-L", libdir, f"-l{name}",
+                    prog, "-o", str(tmp_path / "example"), "-L", libdir, f"-l{name}",
                     f"-Wl,-rpath,{libdir}"], check=True)
 
 

@@ -133,14 +133,15 @@ def test_trilinear_periodic_wrap_and_clamp():
 
 
 def test_features_of_an_affine_flow_give_the_sample_points():
-    # u = A x: feature block s is R^T (A x_s - U) / V, so with R = I it
-    # reveals the sample point x_s = x_C + (1.5a i, 1.5b j, 1.5c k)
+    # u = A x and a translating body: feature block s is R^T (A x_s - U) / V,
+    # so with R = I it reveals the sample point x_s = x_C + (1.5a i, 1.5b j,
+    # 1.5c k)
     dims = (40, 30, 30)
     A = np.diag([1.0, 2.0, 3.0])
     u3 = affine_field(dims, A, np.zeros(3))
     pos, semi, vel = np.array([20.0, 15.0, 15.0]), (6.0, 2.0, 2.0), np.array([0.5, 0.0, -0.25])
     gam = 0.01
-    f = cl.features(u3, dims, (0, 0, 0), pos, (1, 0, 0, 0), vel, semi, gam)
+    f = cl.features(u3, dims, (0, 0, 0), pos, (1, 0, 0, 0), vel, (0, 0, 0), semi, gam)
     V = gam * semi[0]
     s = 0
     for i in (-1, 0, 1):
@@ -152,6 +153,25 @@ def test_features_of_an_affine_flow_give_the_sample_points():
     np.testing.assert_allclose(f[81:], [1, 0, 0, 3.0, 2.0])
 
 
+def test_features_vanish_for_a_body_moving_rigidly_with_the_flow():
+    # the rigid-body field u = U + Omega x (x - x_C) is affine, so its
+    # trilinear interpolation is exact: a body translating with U and rotating
+    # with Omega about x_C sees zero relative velocity at every sample point,
+    # whatever its orientation
+    dims = (40, 36, 38)
+    pos = np.array([19.3, 17.6, 18.2])
+    U, Om = np.array([0.01, -0.004, 0.007]), np.array([0.002, 0.003, -0.001])
+    W = np.array([[0, -Om[2], Om[1]], [Om[2], 0, -Om[0]], [-Om[1], Om[0], 0]])
+    u3 = affine_field(dims, W, U - W @ pos)
+    q = np.array([0.8, 0.2, -0.4, 0.4])
+    q /= np.linalg.norm(q)
+    f = cl.features(u3, dims, (0, 0, 0), pos, q, U, Om, (6.0, 2.0, 1.5), 0.001)
+    np.testing.assert_allclose(f[:81], 0.0, atol=1e-10)
+    # and without the rotation term the same flow leaves Omega x r / V there
+    f0 = cl.features(u3, dims, (0, 0, 0), pos, q, U, (0, 0, 0), (6.0, 2.0, 1.5), 0.001)
+    assert np.abs(f0[:81]).max() > 1.0
+
+
 def test_features_rotate_into_the_body_frame():
     # a uniform flow (1, 0, 0) seen by a body turned 90 degrees about z: its
     # x axis points along world y, so the flow has body components (0, -1, 0)
@@ -159,7 +179,7 @@ def test_features_rotate_into_the_body_frame():
     u3 = np.zeros((3, 8000))
     u3[0] = 1.0
     q = (np.cos(np.pi / 4), 0, 0, np.sin(np.pi / 4))
-    f = cl.features(u3, dims, (1, 1, 1), (10, 10, 10), q, (0, 0, 0), (3, 1, 1), 0.0)
+    f = cl.features(u3, dims, (1, 1, 1), (10, 10, 10), q, (0, 0, 0), (0, 0, 0), (3, 1, 1), 0.0)
     for s in range(27):
         np.testing.assert_allclose(f[3 * s:3 * s + 3], [0, -1, 0], atol=1e-14)
     np.testing.assert_allclose(f[81:84], [0, 1, 0], atol=1e-15)
