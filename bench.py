@@ -38,7 +38,9 @@ BYTES_PER_POP = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
 # kernel, keyed by workload and precision, with the fingerprint of the sweep
 # sources it was taken on; a changed kernel reports no traffic until it is
 # captured again.  Captures are summarised under profiles/.
-SWEEP_SOURCES = ("paper_1503_06869_gb300/csrc/lbm_sweep.cu", "paper_1503_06869_gb300/csrc/lbm_internal.cuh")
+SWEEP_SOURCES = ("paper_1503_06869_gb300/csrc/lbm_sweep.cuh", "paper_1503_06869_gb300/csrc/lbm_sweep.cu",
+                 "paper_1503_06869_gb300/csrc/lbm_sweep_f32.cu", "paper_1503_06869_gb300/csrc/lbm_sweep_f16.cu",
+                 "paper_1503_06869_gb300/csrc/lbm_sweep_bf16.cu", "paper_1503_06869_gb300/csrc/lbm_internal.cuh")
 SWEEP_TRAFFIC = {
     ("shear256x128x128_spheroid24x3x3", "f32"): {"bytes": 570.72e6, "src": "3e5fec48d2252c95",
                                                 "profile": "profiles/sweep_kernel_shear256x128x128_f32.md"},

@@ -269,6 +269,7 @@ typedef struct lbm_info {
     int remap_grid;             /* blocks of that launch (0 when not fused) */
     int cells_per_thread;       /* direct sweep: consecutive cells per thread (1, 2, 4) */
     int device;                 /* CUDA device of the context */
+    int sweep_prefetch;         /* tiles ahead that the direct sweep prefetches into L2 (0: none) */
 } lbm_info;
 
 lbm_status lbm_get_info(lbm_ctx *ctx, lbm_info *info);
@@ -305,6 +306,16 @@ lbm_status lbm_set_cells_per_thread(lbm_ctx *ctx, int cpt);
  * suspensions); the autotuner decides.  Applies to the direct sweep only;
  * takes effect at the next lbm_step. */
 lbm_status lbm_set_sweep_split(lbm_ctx *ctx, int enable);
+
+/* L2 prefetch in the direct sweep (enable != 0; default 0): a block that
+ * starts a tile first asks the L2 for the population ranges of a later tile
+ * (the tile one resident wave ahead, or the block's own next tile on a
+ * persistent grid) with one asynchronous bulk prefetch per population plane,
+ * so that tile's loads find their data in the L2.  A hint only: results do
+ * not change.  Chosen per context by lbm_autotune; takes effect at the next
+ * lbm_step.  No counterpart in the paper (a launch parameter like the block
+ * size). */
+lbm_status lbm_set_sweep_prefetch(lbm_ctx *ctx, int enable);
 
 /* Fused re-mapping step (enable != 0; default 0): the rigid-body update
  * (Sec. 4.3) and the four passes of the obstacle re-mapping (Sec. 4.2:

@@ -44,7 +44,10 @@ struct lbm_ctx {
     uint32_t *nbody = nullptr;      // per-cell first neighbouring body
     uint32_t *near_list = nullptr;  // split direct sweep: compacted near-obstacle cells
     uint32_t *near_count = nullptr;
+    uint32_t *chg = nullptr;        // re-mapping: cells whose owner changed this step
+    uint32_t *chg_n = nullptr;
     bool split = false;             // direct sweep: near-obstacle cells in a kernel of their own
+    bool prefetch = false;          // direct sweep: L2 prefetch of a later tile
     __half *cl_par = nullptr;       // learned closure: FP16 network parameters
     bool closure = false;
     uint32_t *err = nullptr;
@@ -215,6 +218,20 @@ int default_grid(lbm_ctx *ctx) {
     return (int)(g > 0 ? g : 1);
 }
 
+// Tiles ahead of its current one that a direct-sweep block prefetches: its
+// own next tile on a persistent grid, else the tile one resident wave ahead
+// (blocks start roughly in index order, so that tile's block starts about
+// one block's duration later).
+int prefetch_ahead(lbm_ctx *ctx) {
+    if (ctx->grid < ctx->ntiles) return ctx->grid;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int nb = sweep_max_active_blocks(ctx->prec, SWEEP_DIRECT, ctx->block, ctx->cpt);
+    const long long w = (long long)(sms > 0 ? sms : 1) * (nb > 0 ? nb : 1);
+    return (int)(w < ctx->ntiles ? w : ctx->ntiles);
+}
+
 SweepArgs sweep_args(lbm_ctx *ctx) {
     SweepArgs a;
     a.lat0 = ctx->lat_h[0];
@@ -233,6 +250,7 @@ SweepArgs sweep_args(lbm_ctx *ctx) {
     a.nbody = ctx->nbody;
     a.tick = ctx->tick;
     const bool split = ctx->split && ctx->variant == SWEEP_DIRECT;
+    a.pf_ahead = ctx->variant == SWEEP_DIRECT && ctx->prefetch ? prefetch_ahead(ctx) : 0;
     a.near_list = split ? ctx->near_list : nullptr;
     a.near_count = split ? ctx->near_count : nullptr;
     return a;
@@ -273,6 +291,9 @@ RemapArgs remap_args(lbm_ctx *ctx) {
     a.links = ctx->links;
     a.nbody = ctx->nbody;
     a.tick = ctx->tick;
+    a.chg = ctx->chg;
+    a.chg_n = ctx->chg_n;
+    a.chg_cap = ctx->ncells;
     return a;
 }
 
@@ -625,6 +646,8 @@ lbm_status create_common(const lbm_grid_desc *cells, int ncells, lbm_ctx **out) 
     ctx->nbody = (uint32_t *)owned_alloc(ctx, (size_t)coff * 4);
     ctx->near_list = (uint32_t *)owned_alloc(ctx, (size_t)coff * 4);
     ctx->near_count = (uint32_t *)owned_alloc(ctx, 16);
+    ctx->chg = (uint32_t *)owned_alloc(ctx, (size_t)coff * 4);
+    ctx->chg_n = (uint32_t *)owned_alloc(ctx, 16);
     ctx->wall_acc = (double *)owned_alloc(ctx, sizeof(double) * 6 * ACC_COPIES * ncells);
     ctx->wall_last = (double *)owned_alloc(ctx, sizeof(double) * 6 * ncells);
     ctx->err = (uint32_t *)owned_alloc(ctx, 16);
@@ -640,7 +663,7 @@ lbm_status create_common(const lbm_grid_desc *cells, int ncells, lbm_ctx **out) 
     }
     if (!ctx->lat_d || !ctx->f || !ctx->flags || !ctx->pid || !ctx->pid_prev || !ctx->wall_acc ||
         !ctx->wall_last || !ctx->err || !ctx->tick || !ctx->tbits || !ctx->links || !ctx->nbody || !ctx->near_list ||
-        !ctx->near_count || !ctx->gbar || !ctx->stab_acc || !ctx->stab_accf || (ncells > 1 && !ctx->tile_lat)) {
+        !ctx->near_count || !ctx->chg || !ctx->chg_n || !ctx->gbar || !ctx->stab_acc || !ctx->stab_accf || (ncells > 1 && !ctx->tile_lat)) {
         lbm_destroy(ctx);
         return LBM_ERR_OOM;
     }
@@ -658,6 +681,7 @@ lbm_status create_common(const lbm_grid_desc *cells, int ncells, lbm_ctx **out) 
         cudaMemsetAsync(ctx->wall_last, 0, sizeof(double) * 6 * ncells, ctx->stream) != cudaSuccess ||
         cudaMemsetAsync(ctx->err, 0, 16, ctx->stream) != cudaSuccess ||
         cudaMemsetAsync(ctx->tick, 0, 16, ctx->stream) != cudaSuccess ||
+        cudaMemsetAsync(ctx->chg_n, 0, 16, ctx->stream) != cudaSuccess ||
         cudaMemsetAsync(ctx->gbar, 0, 16, ctx->stream) != cudaSuccess ||
         cudaMemsetAsync(ctx->stab_acc, 0, 64, ctx->stream) != cudaSuccess ||
         cudaMemsetAsync(ctx->stab_accf, 0, 16, ctx->stream) != cudaSuccess) {
@@ -1243,6 +1267,7 @@ lbm_status lbm_get_info(lbm_ctx *ctx, lbm_info *info) {
     info->remap_grid = fused_remap(ctx) ? ctx->remap_grid : 0;
     info->cells_per_thread = ctx->variant == SWEEP_DIRECT ? ctx->cpt : 1;
     info->device = ctx->device;
+    info->sweep_prefetch = ctx->variant == SWEEP_DIRECT && ctx->prefetch ? prefetch_ahead(ctx) : 0;
     return LBM_OK;
 }
 
@@ -1297,21 +1322,22 @@ lbm_status lbm_autotune(lbm_ctx *ctx, int *block_out, int *grid_out) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     // candidates: the ring sweep (block 0), the staged sweep (block -1) and
     // the direct sweep at two block sizes with 1, 2 or 4 cells per thread,
-    // fused or split, each with persistent grids (1x, 2x resident) and one
-    // tile per block
+    // fused or split, with and without L2 prefetch, each with persistent
+    // grids (1x, 2x resident) and one tile per block
     struct Cand {
         int block, cpt;
-        bool split;
+        bool split, prefetch;
     };
-    std::vector<Cand> cands = {{0, 1, false}, {-1, 1, false}};
+    std::vector<Cand> cands = {{0, 1, false, false}, {-1, 1, false, false}};
     for (int blk : {128, 256})
         for (int c : {1, 2, 4})
             if (sweep_cpt_supported(ctx->prec, c))
-                for (bool sp : {false, true}) cands.push_back({blk, c, sp});
+                for (bool sp : {false, true})
+                    for (bool pf : {false, true}) cands.push_back({blk, c, sp, pf});
     double best = 1e30;
     int bb = ctx->variant == SWEEP_RING ? 0 : (ctx->variant == SWEEP_STAGED ? -1 : ctx->block);
     int bg = ctx->grid, bc = ctx->cpt;
-    bool bsplit = ctx->split;
+    bool bsplit = ctx->split, bpf = ctx->prefetch;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -1320,6 +1346,7 @@ lbm_status lbm_autotune(lbm_ctx *ctx, int *block_out, int *grid_out) {
         lbm_status s = lbm_set_launch(ctx, cand.block, 0);
         if (s != LBM_OK) break;
         ctx->split = cand.split;
+        ctx->prefetch = cand.prefetch;
         const int occ = sweep_max_active_blocks(ctx->prec, ctx->variant, ctx->block, ctx->cpt);
         if (occ <= 0) continue;
         const int grids[] = {sms * occ, 2 * sms * occ, ctx->ntiles};
@@ -1348,12 +1375,14 @@ lbm_status lbm_autotune(lbm_ctx *ctx, int *block_out, int *grid_out) {
                 bg = gr;
                 bc = cand.cpt;
                 bsplit = ctx->split;
+                bpf = ctx->prefetch;
             }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     ctx->split = bsplit;
+    ctx->prefetch = bpf;
     ctx->cpt = bb > 0 ? bc : 1;
     lbm_status s = lbm_set_launch(ctx, bb, bg);
     CK(cudaMemcpyAsync(ctx->f, backup, fbytes, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -1371,6 +1400,15 @@ lbm_status lbm_set_sweep_split(lbm_ctx *ctx, int enable) {
     DevGuard dg(ctx);
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->split = enable != 0;
+    drop_graph(ctx);
+    return LBM_OK;
+}
+
+lbm_status lbm_set_sweep_prefetch(lbm_ctx *ctx, int enable) {
+    if (!ctx) return LBM_ERR_ARG;
+    DevGuard dg(ctx);
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->prefetch = enable != 0;
     drop_graph(ctx);
     return LBM_OK;
 }

@@ -11,6 +11,7 @@
 // (bodies or samples) and walks the 8-column tiles of every layer with its
 // operands in shared memory.
 #include <cmath>
+#include <mutex>
 
 #include "lbm_internal.cuh"
 
@@ -142,8 +143,8 @@ __device__ __forceinline__ void forward_rows(const NetSmem &s, const __half *X, 
 // fluid cells, zero on wall and particle cells), reading the populations in
 // the AA layout the next sweep (parity NEXT_ODD) expects.
 template <int PREC, int NEXT_ODD>
-__device__ void cell_velocity(const LatDev &L, const void *fv, const uint8_t *flags, int i, int j, int k,
-                              float u[3]) {
+__device__ __forceinline__ void cell_velocity(const LatDev &L, const void *fv, const uint8_t *flags, int i, int j,
+                                              int k, float u[3]) {
     using S = Store<PREC>;
     using T = typename S::T;
     using C = typename S::C;  // FP64 only on FP64 lattices (GB300's FP64 rate is low)
@@ -153,17 +154,23 @@ __device__ void cell_velocity(const LatDev &L, const void *fv, const uint8_t *fl
     const T *base = reinterpret_cast<const T *>(fv) + L.f_off;
     const long long np = L.npad;
     C jx = 0, jy = 0, jz = 0;
+    // odd layout: the neighbours' flag bytes first (all in flight together),
+    // then the populations they select
+    const T *src[Q];
 #pragma unroll
     for (int q = 1; q < Q; ++q) {
-        C g;
         if (!NEXT_ODD) {
-            g = S::ld(base + q * np + x);
+            src[q] = base + q * np + x;
         } else {
             const int zi = wrapi(i - cx(q), L.nx), zj = wrapi(j - cy(q), L.ny), zk = wrapi(k - cz(q), L.nz);
             const int z = zi + L.nx * (zj + L.ny * zk);
-            g = (flags[L.c_off + z] & (F_SOLID | F_FSLIP)) == F_SOLID ? S::ld(base + q * np + x)
-                                                                      : S::ld(base + opp(q) * np + z);
+            src[q] = (flags[L.c_off + z] & (F_SOLID | F_FSLIP)) == F_SOLID ? base + q * np + x
+                                                                           : base + opp(q) * np + z;
         }
+    }
+#pragma unroll
+    for (int q = 1; q < Q; ++q) {
+        const C g = S::ld(src[q]);
         if (cx(q)) jx += cx(q) > 0 ? g : -g;
         if (cy(q)) jy += cy(q) > 0 ? g : -g;
         if (cz(q)) jz += cz(q) > 0 ? g : -g;
@@ -174,78 +181,86 @@ __device__ void cell_velocity(const LatDev &L, const void *fv, const uint8_t *fl
     u[2] = (float)(jz * lp.inv_rho0 + C(0.5) * lp.g[2]);
 }
 
-// One warp per body.  Lane s < 27 interpolates the velocity at sample point
-// s (offsets (1.5 a i, 1.5 b j, 1.5 c k), s = 9(i+1) + 3(j+1) + (k+1)) from
-// its 8 surrounding cells (periodic axes wrap, the others clamp), subtracts
-// the body's rigid motion continued to that point (U + Omega x R o_s),
-// rotates into the body frame and scales by 1/(shear rate * a); lanes 27 and
-// 28 write the body axis, a/b and b.
+// One block of FEAT_THREADS threads per body: thread t < 216 takes corner
+// t % 8 of sample point s = t / 8 (offsets (1.5 a i, 1.5 b j, 1.5 c k),
+// s = 9(i+1) + 3(j+1) + (k+1)), the cell of that corner of the point's
+// surrounding cube (periodic axes wrap, the others clamp) and its trilinear
+// weight; the eight corners of a point are eight consecutive lanes and sum
+// their weighted velocities by shuffles.  The corner-0 lane subtracts the
+// body's rigid motion continued to the point (U + Omega x R o_s), rotates
+// into the body frame and scales by 1/(shear rate * a); threads 216 and 217
+// write the body axis, a/b and b.  A corner per thread keeps eight times as
+// many cell reads in flight as a point per thread.
+constexpr int FEAT_THREADS = 224;
+
 template <int PREC, int NEXT_ODD>
-__global__ void closure_features_kernel(ClosureArgs a) {
+__global__ void __launch_bounds__(FEAT_THREADS) closure_features_kernel(ClosureArgs a) {
     pdl_enter();
-    const int p = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
+    const int p = (int)blockIdx.x;
+    const int t = (int)threadIdx.x;
     const PartDev &P = a.P;
-    if (p >= P.np) return;
+    if (p >= P.np) return;  // uniform per block
     const LatDev &L = a.lat[P.cell[p]];
     const float *bf = P.bodyf + BF_STRIDE * (size_t)p;
-    float R[9], pos[3], U[3], W[3];
+    float R[9], pos[3];
     for (int k = 0; k < 9; ++k) R[k] = bf[BF_R + k];
-    for (int k = 0; k < 3; ++k) {
-        pos[k] = bf[BF_POS + k] + bf[BF_POSLO + k];
-        U[k] = bf[BF_U + k];
-        W[k] = bf[BF_W + k];
-    }
+    for (int k = 0; k < 3; ++k) pos[k] = bf[BF_POS + k] + bf[BF_POSLO + k];
     const float sa = (float)P.semi[3 * (size_t)p], sb = (float)P.semi[3 * (size_t)p + 1],
                 sc = (float)P.semi[3 * (size_t)p + 2];
     float *out = a.feat + (size_t)p * NIN;
-    if (lane < 27) {
-        const int i = lane / 9 - 1, j = (lane / 3) % 3 - 1, k = lane % 3 - 1;
+    const int s = t >> 3, corner = t & 7;
+    float ro[3] = {0.f, 0.f, 0.f}, u[3] = {0.f, 0.f, 0.f};
+    if (s < 27) {
+        const int i = s / 9 - 1, j = (s / 3) % 3 - 1, k = s % 3 - 1;
         const float o[3] = {1.5f * sa * i, 1.5f * sb * j, 1.5f * sc * k};
-        float x[3], ro[3];
+        float x[3];
         for (int r = 0; r < 3; ++r) {
             ro[r] = R[3 * r] * o[0] + R[3 * r + 1] * o[1] + R[3 * r + 2] * o[2];
             x[r] = pos[r] + ro[r];
         }
         const int dims[3] = {L.nx, L.ny, L.nz}, per[3] = {L.px, L.py, L.pz};
-        int i0[3];
-        float w1[3];
+        int idx[3];
+        float w = 1.f;
         for (int r = 0; r < 3; ++r) {
             const float fl = floorf(x[r]);
-            i0[r] = (int)fl;
-            w1[r] = x[r] - fl;
-        }
-        float u[3] = {0.f, 0.f, 0.f};
-        for (int c = 0; c < 8; ++c) {
-            int idx[3];
-            float w = 1.f;
-            for (int r = 0; r < 3; ++r) {
-                const int off = (c >> r) & 1;
-                w *= off ? w1[r] : 1.f - w1[r];
-                int v = i0[r] + off;
-                if (per[r]) {
-                    v %= dims[r];
-                    if (v < 0) v += dims[r];
-                } else {
-                    v = min(max(v, 0), dims[r] - 1);
-                }
-                idx[r] = v;
+            const float w1 = x[r] - fl;
+            const int off = (corner >> r) & 1;
+            w *= off ? w1 : 1.f - w1;
+            int v = (int)fl + off;
+            if (per[r]) {
+                v %= dims[r];
+                if (v < 0) v += dims[r];
+            } else {
+                v = min(max(v, 0), dims[r] - 1);
             }
-            float uc[3];
-            cell_velocity<PREC, NEXT_ODD>(L, a.f, a.flags, idx[0], idx[1], idx[2], uc);
-            for (int r = 0; r < 3; ++r) u[r] += w * uc[r];
+            idx[r] = v;
+        }
+        float uc[3];
+        cell_velocity<PREC, NEXT_ODD>(L, a.f, a.flags, idx[0], idx[1], idx[2], uc);
+        for (int r = 0; r < 3; ++r) u[r] = w * uc[r];
+    }
+    // corners 0..7 of a point are lanes 8m .. 8m+7 of one warp: a butterfly
+    // over them sums the eight weighted velocities (pairwise, in FP32)
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1)
+        for (int r = 0; r < 3; ++r) u[r] += __shfl_xor_sync(0xffffffffu, u[r], o);
+    if (s < 27 && corner == 0) {
+        float U[3], W[3];
+        for (int k = 0; k < 3; ++k) {
+            U[k] = bf[BF_U + k];
+            W[k] = bf[BF_W + k];
         }
         const float V = L.cl_gamma > 0.f ? L.cl_gamma * sa : 1.f;
         // relative to the rigid motion continued to the sample point
         const float d[3] = {u[0] - (U[0] + (W[1] * ro[2] - W[2] * ro[1])),
                             u[1] - (U[1] + (W[2] * ro[0] - W[0] * ro[2])),
                             u[2] - (U[2] + (W[0] * ro[1] - W[1] * ro[0]))};
-        for (int r = 0; r < 3; ++r) out[3 * lane + r] = (R[r] * d[0] + R[3 + r] * d[1] + R[6 + r] * d[2]) / V;
-    } else if (lane == 27) {
+        for (int r = 0; r < 3; ++r) out[3 * s + r] = (R[r] * d[0] + R[3 + r] * d[1] + R[6 + r] * d[2]) / V;
+    } else if (t == 216) {
         out[81] = R[0];
         out[82] = R[3];
         out[83] = R[6];
-    } else if (lane == 28) {
+    } else if (t == 217) {
         out[84] = sa / sb;
         out[85] = sb;
     }
@@ -465,11 +480,32 @@ cudaError_t set_smem(K kernel, size_t bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// The dynamic shared memory limit is a per-device attribute of a kernel:
+// raised once per device (done[d]), under one mutex (launches come from any
+// host thread, each context on its own device).
+constexpr int SMEM_MAX_DEVICES = 64;
+inline std::mutex &smem_mu() {
+    static std::mutex m;
+    return m;
+}
+template <class K>
+cudaError_t set_smem_once(K kernel, size_t bytes, bool (&done)[SMEM_MAX_DEVICES]) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= SMEM_MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(smem_mu());
+    if (!done[dev]) {
+        if ((e = set_smem(kernel, bytes)) != cudaSuccess) return e;
+        done[dev] = true;
+    }
+    return cudaSuccess;
+}
+
 template <int PREC>
 cudaError_t features_prec(int next_odd, const ClosureArgs &a, int np, cudaStream_t s) {
-    const int blocks = (int)((32ll * np + 255) / 256);
-    return next_odd ? launch_pdl(closure_features_kernel<PREC, 1>, blocks, 256, 0, s, a)
-                    : launch_pdl(closure_features_kernel<PREC, 0>, blocks, 256, 0, s, a);
+    return next_odd ? launch_pdl(closure_features_kernel<PREC, 1>, np, FEAT_THREADS, 0, s, a)
+                    : launch_pdl(closure_features_kernel<PREC, 0>, np, FEAT_THREADS, 0, s, a);
 }
 
 }  // namespace
@@ -493,29 +529,20 @@ cudaError_t launch_mlp_infer(const MlpArgs &m, const ClosureArgs *apply, cudaStr
     const int blocks = (m.n + ROWS - 1) / ROWS;
     cudaError_t e;
     if (apply) {
-        static bool attr = false;
-        if (!attr) {
-            if ((e = set_smem(mlp_infer_kernel<true>, smem)) != cudaSuccess) return e;
-            attr = true;
-        }
+        static bool attr[SMEM_MAX_DEVICES] = {};
+        if ((e = set_smem_once(mlp_infer_kernel<true>, smem, attr)) != cudaSuccess) return e;
         return launch_pdl(mlp_infer_kernel<true>, blocks, 256, smem, s, m, *apply);
     }
-    static bool attr = false;
-    if (!attr) {
-        if ((e = set_smem(mlp_infer_kernel<false>, smem)) != cudaSuccess) return e;
-        attr = true;
-    }
+    static bool attr[SMEM_MAX_DEVICES] = {};
+    if ((e = set_smem_once(mlp_infer_kernel<false>, smem, attr)) != cudaSuccess) return e;
     return launch_pdl(mlp_infer_kernel<false>, blocks, 256, smem, s, m, ClosureArgs{});
 }
 
 cudaError_t launch_mlp_grad(const MlpArgs &m, cudaStream_t s) {
     const size_t smem = sizeof(TrainSmem);
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = set_smem(mlp_grad_kernel, smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static bool attr[SMEM_MAX_DEVICES] = {};
+    cudaError_t e = set_smem_once(mlp_grad_kernel, smem, attr);
+    if (e != cudaSuccess) return e;
     return launch_pdl(mlp_grad_kernel, 1, 256, smem, s, m);
 }
 

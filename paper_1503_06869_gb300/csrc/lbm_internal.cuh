@@ -184,6 +184,9 @@ struct SweepArgs {
     uint32_t *near_count;
     const int *tile_lat;     // batches: lattice of every tile (null: binary search on tile0)
     const uint32_t *tick;    // step counter (seed of the BF16 stochastic rounding)
+    // direct sweep: a block starting tile t asks the L2 to fetch the
+    // population ranges of tile t + pf_ahead (0: no prefetch)
+    int pf_ahead;
 };
 
 // Stochastic rounding of the BF16 sweep stores.  A bfloat16 keeps 8
@@ -450,6 +453,12 @@ struct RemapArgs {
     uint64_t *links;     // per-cell link words (LK_* layout)
     uint32_t *nbody;     // per-cell first neighbouring body
     uint32_t *tick;      // step counter, advanced once per rigid-body update
+    // cells whose owner changed in this step's uncover / claim passes, each
+    // listed once (the pass that sets its F_CHANGED bit lists it); the
+    // rigid-body update empties the list.  chg_cap: the arena's cell count
+    uint32_t *chg;
+    uint32_t *chg_n;
+    long long chg_cap;
 };
 // Recount every tile bit from the flags (bit t = tile t holds a nonzero flag).
 cudaError_t launch_tile_bits(const RemapArgs &a, int ntiles, cudaStream_t s);

@@ -212,6 +212,7 @@ __device__ void rigid_unit(const RemapArgs &a, int warp, int lane) {
     }
     const size_t t = (size_t)warp;
     if (lane == 0) P.changed[t] = 0;  // set again by this step's uncover / claim passes
+    if (t == 0 && lane == 0 && a.chg_n) *a.chg_n = 0;  // the step's changed-cell list starts empty
     const int k = lane < 3 ? lane : 0;  // vector component of this lane (lanes >= 3 mirror 0, store nothing)
     const bool vec = lane < 3;
     // ---- loads
@@ -394,15 +395,22 @@ __device__ __forceinline__ int modc(int v, int n) {
     return m < 0 ? m + n : m;
 }
 
-__device__ __forceinline__ bool region_cell(const int *reg, const LatDev &L, int r, RegionCell &c) {
-    const int e0 = reg[3], e1 = reg[4];
-    const int r0 = r % e0, r12 = r / e0;
-    const int r1 = r12 % e1, r2 = r12 / e1;
-    c.i = modc(reg[0] + r0, L.nx);
-    c.j = modc(reg[1] + r1, L.ny);
-    c.k = modc(reg[2] + r2, L.nz);
+// v mod n for v in [-n, 2n) without a division (a box origin lies within one
+// period of its body's wrapped centre and a box spans at most one period),
+// with the division kept for any other v.
+__device__ __forceinline__ int wrap_box(int v, int n) {
+    if (v >= 0 && v < n) return v;
+    if (v < 0 && v >= -n) return v + n;
+    if (v >= n && v < 2 * n) return v - n;
+    return modc(v, n);
+}
+
+// Cell of a box from its box coordinates (r0 along x, row r1 + e1 r2).
+__device__ __forceinline__ void box_cell(const int *reg, const LatDev &L, int r0, int r1, int r2, RegionCell &c) {
+    c.i = wrap_box(reg[0] + r0, L.nx);
+    c.j = wrap_box(reg[1] + r1, L.ny);
+    c.k = wrap_box(reg[2] + r2, L.nz);
     c.idx = c.i + L.nx * (c.j + L.ny * c.k);
-    return true;
 }
 
 // Cells of a re-mapping box that the passes visit: the box's rows (y, z) and
@@ -450,11 +458,12 @@ __device__ __forceinline__ void row_interval(const int *reg, const float *bf, in
     x1 = min(reg[3] - 1, (int)fminf(ceilf(cx + hi) + 1.0f, (float)reg[3]));
 }
 
+// Threads per block of the re-mapping passes.
+constexpr int REMAP_BLOCK = 256;
+
 // The region passes work on np * bpb units of one block each: unit u covers
 // body p = u / bpb.  The separate kernels run one unit per block; the fused
-// kernel loops its blocks over the units.  The warps of a body's units take
-// the box's rows in turn; the lanes of a warp share the row's cells in the
-// cylinder's interval.
+// kernel loops its blocks over the units.
 struct RegionLoop {
     int p, first, stride;
 };
@@ -465,6 +474,74 @@ __device__ __forceinline__ RegionLoop region_loop(int unit, int bpb) {
     l.first = (unit % bpb) * blockDim.x + threadIdx.x;
     l.stride = bpb * blockDim.x;
     return l;
+}
+
+// The cells of a box that lie in its rows' cylinder intervals, each handed
+// once to f(r0, r1, r2) (box coordinates: r0 along x, row r1 + e1 r2, e1 the
+// box's extent in y).  The warps of a body's units take the box's rows in
+// batches of up to 32 (fewer when the box has fewer than 32 rows per warp,
+// so that every warp gets rows): each lane of a batch finds the interval of
+// one row, a warp prefix sum lays the rows' cells end to end, and
+// the lanes take that list 32 cells at a time (a lane finds the row of its
+// cell by binary search over the prefix sums), so a short row does not leave
+// most of a warp idle and a row missing the cylinder costs one lane's
+// interval test.  Called by whole warps; f runs on the lanes that hold a
+// cell.  f returns a cell (index in the flag arena) to append to the step's
+// changed-cell list, or -1; the warp appends its cells with one atomic.
+template <class F>
+__device__ __forceinline__ void for_tube_cells(const RemapArgs &a, const int *reg, const float *bfp,
+                                               const RegionLoop &rl, F &&f) {
+    constexpr unsigned FULL = 0xffffffffu;
+    const int rows = reg[4] * reg[5];
+    const int lane = threadIdx.x & 31;
+    const int nw = rl.stride >> 5;
+    const int batch = min(32, max(1, (rows + nw - 1) / nw));
+    for (int rb = (rl.first >> 5) * batch; rb < rows; rb += nw * batch) {
+        const int r = rb + lane;
+        const int r1 = r % reg[4], r2 = r / reg[4];
+        int x0 = 0, x1 = -1;
+        if (lane < batch && r < rows) row_interval(reg, bfp, r1, r2, x0, x1);
+        const int len = x1 >= x0 ? x1 - x0 + 1 : 0;
+        int incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int total = __shfl_sync(FULL, incl, 31);
+        for (int jb = 0; jb < total; jb += 32) {
+            const int j = jb + lane;
+            // row of cell j: the first lane whose inclusive sum exceeds j
+            int l = 0;
+#pragma unroll
+            for (int b = 16; b; b >>= 1) {
+                const int v = __shfl_sync(FULL, incl, l + b - 1);
+                if (v <= j) l += b;
+            }
+            l = l < 31 ? l : 31;
+            const int rx0 = __shfl_sync(FULL, x0, l);
+            const int rstart = __shfl_sync(FULL, incl - len, l);
+            const int c1 = __shfl_sync(FULL, r1, l), c2 = __shfl_sync(FULL, r2, l);
+            long long add = -1;
+            if (j < total) add = f(rx0 + (j - rstart), c1, c2);
+            const unsigned bal = __ballot_sync(FULL, add >= 0);
+            if (bal && a.chg) {
+                uint32_t base = 0;
+                if (lane == 0) base = atomicAdd(a.chg_n, (uint32_t)__popc(bal));
+                base = __shfl_sync(FULL, base, 0) + (uint32_t)__popc(bal & ((1u << lane) - 1u));
+                if (add >= 0 && (long long)base < a.chg_cap) a.chg[base] = (uint32_t)add;
+            }
+        }
+    }
+}
+
+// Sets F_CHANGED on cell cg (flag byte) and tells whether this call set it:
+// an atomic OR on the byte's 32-bit word (the passes touch flag bytes only
+// through this), so a cell changed by several bodies is listed once.
+__device__ __forceinline__ bool mark_changed(uint8_t *flags, long long cg) {
+    uint32_t *word = reinterpret_cast<uint32_t *>(flags + (cg & ~3ll));
+    const uint32_t bit = (uint32_t)F_CHANGED << (8 * (int)(cg & 3));
+    return !(atomicOr(word, bit) & bit);
 }
 
 template <int PASS>
@@ -481,37 +558,38 @@ __device__ void remap_region(const RemapArgs &a, int unit, int bpb) {
     BodyF32 bf;
     const float *bfp = P.bodyf + BF_STRIDE * (size_t)p;
     load_body_f32(bfp, bf);
-    const int rows = reg[4] * reg[5];
-    const int lane = threadIdx.x & 31;
-    for (int rr = rl.first >> 5; rr < rows; rr += rl.stride >> 5) {
-      int x0, x1;
-      row_interval(reg, bfp, rr % reg[4], rr / reg[4], x0, x1);
-      for (int r0 = x0 + lane; r0 <= x1; r0 += 32) {
+    for_tube_cells(a, reg, bfp, rl, [&](int r0, int r1, int r2) -> long long {
         RegionCell c;
-        region_cell(reg, L, r0 + reg[3] * rr, c);
+        box_cell(reg, L, r0, r1, r2, c);
         const long long cg = L.c_off + c.idx;
         if (PASS == 0) {  // uncover
             if (a.pid[cg] == (uint32_t)p && !inside_fast(L, pos, R64, semi, bf, c.i, c.j, c.k)) {
                 a.pid[cg] = PID_FLUID;
                 a.pid_prev[cg] = (uint32_t)p;
-                a.flags[cg] |= F_CHANGED;
                 P.changed[p] = 1;
+                return mark_changed(a.flags, cg) ? cg : -1;
             }
         } else {  // claim
-            if (!(a.flags[cg] & F_WALL) && inside_fast(L, pos, R64, semi, bf, c.i, c.j, c.k)) {
+            // a cell of this body (still inside: the uncover pass ran) or of
+            // a lower-index body (which keeps it) needs no test, nor a wall cell
+            const uint32_t cur = a.pid[cg];
+            if (cur <= (uint32_t)p || (cur >= PID_WALL && cur != PID_FLUID)) return -1;
+            if (inside_fast(L, pos, R64, semi, bf, c.i, c.j, c.k)) {
                 const uint32_t old = atomicMin(&a.pid[cg], (uint32_t)p);
-                if (old == PID_FLUID) a.flags[cg] |= F_CHANGED;
                 // a new obstacle cell, or one taken from a higher-index body
                 // (the neighbours' first-body links change)
-                if (old > (uint32_t)p) P.changed[p] = 1;
+                if (old > (uint32_t)p) {
+                    P.changed[p] = 1;
+                    return mark_changed(a.flags, cg) ? cg : -1;
+                }
             }
         }
-      }
-    }
+        return -1;
+    });
 }
 
 template <int PASS>
-__global__ void remap_region_kernel(RemapArgs a, int bpb) {
+__global__ void __launch_bounds__(REMAP_BLOCK, 4) remap_region_kernel(RemapArgs a, int bpb) {
     pdl_enter();
     remap_region<PASS>(a, blockIdx.x, bpb);
 }
@@ -621,26 +699,21 @@ __device__ void fixup_region(const RemapArgs &a, int unit, int bpb) {
     const int *reg = P.region + 6 * p;
     const float *bfp = P.bodyf + BF_STRIDE * (size_t)p;
     const LatDev &L = a.lat[P.cell[p]];
-    const int rows = reg[4] * reg[5];
-    const int lane = threadIdx.x & 31;
-    for (int rr = rl.first >> 5; rr < rows; rr += rl.stride >> 5) {
-        int x0, x1;
-        row_interval(reg, bfp, rr % reg[4], rr / reg[4], x0, x1);
-        for (int r0 = x0 + lane; r0 <= x1; r0 += 32) {
-            RegionCell c;
-            region_cell(reg, L, r0 + reg[3] * rr, c);
-            const long long cg = L.c_off + c.idx;
-            if (!(a.flags[cg] & F_CHANGED)) continue;
-            const bool old_f = !(a.flags[cg] & F_SOLID);
-            const uint32_t id = a.pid[cg];
-            const bool new_f = id == PID_FLUID;
-            if (old_f == new_f) continue;
-            // exactly one body handles each changed cell: its uncoverer or its new owner
-            const uint32_t owner = new_f ? a.pid_prev[cg] : id;
-            if (owner != (uint32_t)p) continue;
-            fixup_cell<PREC, NEXT_ODD>(a, L, c.i, c.j, c.k, false);
-        }
-    }
+    for_tube_cells(a, reg, bfp, rl, [&](int r0, int r1, int r2) -> long long {
+        RegionCell c;
+        box_cell(reg, L, r0, r1, r2, c);
+        const long long cg = L.c_off + c.idx;
+        if (!(a.flags[cg] & F_CHANGED)) return -1;
+        const bool old_f = !(a.flags[cg] & F_SOLID);
+        const uint32_t id = a.pid[cg];
+        const bool new_f = id == PID_FLUID;
+        if (old_f == new_f) return -1;
+        // exactly one body handles each changed cell: its uncoverer or its new owner
+        const uint32_t owner = new_f ? a.pid_prev[cg] : id;
+        if (owner != (uint32_t)p) return -1;
+        fixup_cell<PREC, NEXT_ODD>(a, L, c.i, c.j, c.k, false);
+        return -1;
+    });
 }
 
 template <int PREC, int NEXT_ODD>
@@ -715,36 +788,113 @@ __device__ void flags_region(const RemapArgs &a, int unit, int bpb) {
     const int *reg = P.region + 6 * p;
     const float *bfp = P.bodyf + BF_STRIDE * (size_t)p;
     const LatDev &L = a.lat[P.cell[p]];
-    const int rows = reg[4] * reg[5];
-    const int lane = threadIdx.x & 31;
-    for (int rr = rl.first >> 5; rr < rows; rr += rl.stride >> 5) {
-        int x0, x1;
-        row_interval(reg, bfp, rr % reg[4], rr / reg[4], x0, x1);
-        for (int r0 = x0 + lane; r0 <= x1; r0 += 32) {
-            RegionCell c;
-            region_cell(reg, L, r0 + reg[3] * rr, c);
-            const long long cg = L.c_off + c.idx;
-            if (a.flags[cg] & F_WALL) continue;
-            uint64_t lk;
-            uint32_t p0;
-            const uint8_t f = flag_of(L, a.pid, L.c_off, c.i, c.j, c.k, lk, p0);
-            a.flags[cg] = f;
-            a.links[cg] = lk;
-            a.nbody[cg] = p0;
-            // a cell turning non-bulk marks its tile; marks are cleared only by a
-            // recount (launch_tile_bits), so a stale mark costs the flagged path,
-            // never a missed cell
-            if (f && a.tbits) {
-                const int t = L.tile0 + c.idx / a.tile;
-                atomicOr(a.tbits + (t >> 5), 1u << (t & 31));
-            }
+    for_tube_cells(a, reg, bfp, rl, [&](int r0, int r1, int r2) -> long long {
+        RegionCell c;
+        box_cell(reg, L, r0, r1, r2, c);
+        const long long cg = L.c_off + c.idx;
+        if (a.flags[cg] & F_WALL) return -1;
+        uint64_t lk;
+        uint32_t p0;
+        const uint8_t f = flag_of(L, a.pid, L.c_off, c.i, c.j, c.k, lk, p0);
+        a.flags[cg] = f;
+        a.links[cg] = lk;
+        a.nbody[cg] = p0;
+        // a cell turning non-bulk marks its tile; marks are cleared only by a
+        // recount (launch_tile_bits), so a stale mark costs the flagged path,
+        // never a missed cell
+        if (f && a.tbits) {
+            const int t = L.tile0 + c.idx / a.tile;
+            atomicOr(a.tbits + (t >> 5), 1u << (t & 31));
         }
-    }
+        return -1;
+    });
 }
 
 __global__ void flags_region_kernel(RemapArgs a, int bpb) {
     pdl_enter();
     flags_region(a, blockIdx.x, bpb);
+}
+
+// The fix-up and flags passes over the step's changed-cell list (the
+// separate launches; the fused kernel keeps the passes over the boxes): every
+// cell whose owner changed is listed once, and only it and its neighbours can
+// need new populations, flags or link words.
+struct ListedCell {
+    const LatDev *L;
+    int i, j, k, idx;
+};
+
+__device__ __forceinline__ ListedCell listed_cell(const RemapArgs &a, uint32_t cell) {
+    int li = 0;
+    if (a.nlat > 1) {
+        int lo = 0, hi = a.nlat - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.lat[mid].c_off <= (long long)cell) lo = mid; else hi = mid - 1;
+        }
+        li = lo;
+    }
+    ListedCell c;
+    c.L = a.lat + li;
+    c.idx = (int)((long long)cell - c.L->c_off);
+    const uint32_t yz = c.L->divx.div((uint32_t)c.idx);
+    c.i = c.idx - (int)yz * c.L->nx;
+    c.k = (int)c.L->divxy.div((uint32_t)c.idx);
+    c.j = (int)yz - c.k * c.L->ny;
+    return c;
+}
+
+__device__ __forceinline__ uint32_t changed_count(const RemapArgs &a) {
+    const uint32_t n = *a.chg_n;
+    return (long long)n < a.chg_cap ? n : (uint32_t)a.chg_cap;
+}
+
+// Pass C over the list: one thread per changed cell.
+template <int PREC, int NEXT_ODD>
+__global__ void fixup_list_kernel(RemapArgs a) {
+    pdl_enter();
+    const uint32_t n = changed_count(a);
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const uint32_t cell = a.chg[t];
+        const bool old_f = !(a.flags[cell] & F_SOLID);
+        const bool new_f = a.pid[cell] == PID_FLUID;
+        if (old_f == new_f) continue;  // owner changed between bodies: populations stay dropped
+        const ListedCell c = listed_cell(a, cell);
+        fixup_cell<PREC, NEXT_ODD>(a, *c.L, c.i, c.j, c.k, false);
+    }
+}
+
+// Pass D over the list: one thread per (changed cell, direction q), for the
+// cell x + c_q (q = 0: the cell itself); a cell next to several changed cells
+// is recomputed by several threads, which write the same values.  Neighbours
+// outside a non-periodic lattice face are skipped (wall layers keep their
+// flags).
+__global__ void flags_list_kernel(RemapArgs a) {
+    pdl_enter();
+    const uint32_t n = changed_count(a);
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n * Q; t += gridDim.x * blockDim.x) {
+        const uint32_t cell = a.chg[t / Q];
+        const int q = (int)(t % Q);
+        const ListedCell c = listed_cell(a, cell);
+        const LatDev &L = *c.L;
+        const int i = c.i + cx(q), j = c.j + cy(q), k = c.k + cz(q);
+        if ((!L.px && (i < 0 || i >= L.nx)) || (!L.py && (j < 0 || j >= L.ny)) || (!L.pz && (k < 0 || k >= L.nz)))
+            continue;
+        const int wi = wrapc(i, L.nx), wj = wrapc(j, L.ny), wk = wrapc(k, L.nz);
+        const int idx = wi + L.nx * (wj + L.ny * wk);
+        const long long cg = L.c_off + idx;
+        if (a.flags[cg] & F_WALL) continue;
+        uint64_t lk;
+        uint32_t p0;
+        const uint8_t f = flag_of(L, a.pid, L.c_off, wi, wj, wk, lk, p0);
+        a.flags[cg] = f;
+        a.links[cg] = lk;
+        a.nbody[cg] = p0;
+        if (f && a.tbits) {
+            const int tt = L.tile0 + idx / a.tile;
+            atomicOr(a.tbits + (tt >> 5), 1u << (tt & 31));
+        }
+    }
 }
 
 // Grid-wide barrier of the fused re-mapping kernel, whose blocks are all
@@ -784,7 +934,6 @@ __device__ bool grid_barrier(GridBar *b, uint32_t *err) {
     return ok != 0;
 }
 
-constexpr int REMAP_BLOCK = 256;
 
 // The whole re-mapping step in one cooperative launch: rigid-body update of
 // every body (and wall hand-over), then uncover, claim, population fix-up and
@@ -1139,10 +1288,19 @@ cudaError_t remap_step_prec(int next_parity, const RemapArgs &a, int bpb, cudaSt
     const unsigned grid = (unsigned)bpb * (unsigned)a.P.np;
     cudaError_t e = launch_pdl(remap_region_kernel<0>, grid, REMAP_BLOCK, 0, s, a, bpb);
     if (e == cudaSuccess) e = launch_pdl(remap_region_kernel<1>, grid, REMAP_BLOCK, 0, s, a, bpb);
+    // the list passes: each thread strides over the list (its length is known
+    // on the device only); the changed cells scale with the bodies, so the
+    // grid is the region passes' (one box's blocks per body), at most about
+    // one wave
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned wave = (unsigned)(sms > 0 ? sms : 1) * 8u;
+    const unsigned lgrid = grid < wave ? grid : wave;
     if (e == cudaSuccess)
-        e = next_parity ? launch_pdl(fixup_region_kernel<PREC, 1>, grid, REMAP_BLOCK, 0, s, a, bpb)
-                        : launch_pdl(fixup_region_kernel<PREC, 0>, grid, REMAP_BLOCK, 0, s, a, bpb);
-    if (e == cudaSuccess) e = launch_pdl(flags_region_kernel, grid, REMAP_BLOCK, 0, s, a, bpb);
+        e = next_parity ? launch_pdl(fixup_list_kernel<PREC, 1>, lgrid, REMAP_BLOCK, 0, s, a)
+                        : launch_pdl(fixup_list_kernel<PREC, 0>, lgrid, REMAP_BLOCK, 0, s, a);
+    if (e == cudaSuccess) e = launch_pdl(flags_list_kernel, lgrid, REMAP_BLOCK, 0, s, a);
     return e;
 }
 

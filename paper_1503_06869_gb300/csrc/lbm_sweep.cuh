@@ -136,6 +136,83 @@ __device__ __forceinline__ void collide_lat(C (&g)[Q], const LatDev &L) {
     }
 }
 
+// The same collision for two cells at once (x: one cell, y: the next), on
+// Blackwell's paired FP32 instructions (one fused multiply-add, add or
+// multiply for both cells per issue slot): the grouped sweep's bulk path is
+// bound by instruction issue in the 16-bit storage forms, and the collision
+// is most of its arithmetic.  Every operation is explicitly rounded, so the
+// results agree with the one-cell collision to rounding (the compiler's
+// contraction choices there may differ).
+__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p_sub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 p_bc(float a) { return make_float2(a, a); }
+
+__device__ __forceinline__ void collide2(float2 (&g)[Q], const float (&k)[11], const float (&fs)[9], float inv,
+                                         float bx, float by, float bz) {
+    float2 s[9], d[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        s[i] = p_add(g[2 * i + 1], g[2 * i + 2]);
+        d[i] = p_sub(g[2 * i + 1], g[2 * i + 2]);
+    }
+    const float2 dr = p_add(g[0], p_add(p_add(p_add(p_add(s[0], s[1]), p_add(s[2], s[3])),
+                                              p_add(p_add(s[4], s[5]), p_add(s[6], s[7]))), s[8]));
+    // momentum components: signed sums of the pair differences (the first
+    // term of each starts the sum, so no zero is added)
+    float2 j[3];
+    bool started[3] = {false, false, false};
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int q = 2 * i + 1;
+        const int c[3] = {cx(q), cy(q), cz(q)};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (!c[a]) continue;
+            if (!started[a]) {
+                j[a] = c[a] > 0 ? d[i] : make_float2(-d[i].x, -d[i].y);
+                started[a] = true;
+            } else {
+                j[a] = c[a] > 0 ? p_add(j[a], d[i]) : p_sub(j[a], d[i]);
+            }
+        }
+    }
+    const float2 ux = p_fma(j[0], p_bc(inv), p_bc(-bx)), uy = p_fma(j[1], p_bc(inv), p_bc(-by)),
+                 uz = p_fma(j[2], p_bc(inv), p_bc(-bz));
+    const float2 base = p_fma(p_bc(k[2]), p_fma(ux, ux, p_fma(uy, uy, p_mul(uz, uz))), dr);
+    g[0] = p_fma(p_bc(k[0]), g[0], p_mul(p_bc(k[1]), base));
+    const float2 e1 = p_mul(p_bc(k[5]), base), e2 = p_mul(p_bc(k[6]), base);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int q = 2 * i + 1;
+        const bool axis = q <= 6;
+        const float2 u[3] = {ux, uy, uz};
+        const int c[3] = {cx(q), cy(q), cz(q)};
+        float2 cu = make_float2(0.f, 0.f);
+        bool first = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (!c[a]) continue;
+            if (first) {
+                cu = c[a] > 0 ? u[a] : make_float2(-u[a].x, -u[a].y);
+                first = false;
+            } else {
+                cu = c[a] > 0 ? p_add(cu, u[a]) : p_sub(cu, u[a]);
+            }
+        }
+        const float2 even = p_fma(p_bc(k[3]), s[i], p_fma(p_bc(axis ? k[7] : k[8]), p_mul(cu, cu), axis ? e1 : e2));
+        const float2 odd = p_fma(p_bc(k[4]), d[i], p_fma(p_bc(axis ? k[9] : k[10]), cu, p_bc(fs[i])));
+        g[q] = p_add(even, odd);
+        g[q + 1] = p_sub(even, odd);
+    }
+}
+
+__device__ __forceinline__ void collide2_lat(float2 (&g)[Q], const LatDev &L) {
+    const float bx = L.ubarf ? L.ubarf[0] : 0.0f, by = L.ubarf ? L.ubarf[1] : 0.0f, bz = L.ubarf ? L.ubarf[2] : 0.0f;
+    collide2(g, L.kf, L.fsf, L.finv_rho0, bx, by, bz);
+}
+
 struct CellGeom {
     int x, y, z;
     int dxm, dxp, dym, dyp, dzm, dzp;  // neighbour offsets with periodic wrap
@@ -181,6 +258,30 @@ __device__ __forceinline__ int tile_lattice(const SweepArgs &a, int tile) {
         if (a.lat[mid].tile0 <= tile) lo = mid; else hi = mid - 1;
     }
     return lo;
+}
+
+// L2 prefetch of the populations a later tile of the direct sweep reads
+// (cp.async.bulk.prefetch: one asynchronous bulk request per plane, no
+// registers held, no completion to wait for).  Thread q < 19 of the block
+// covers plane q: on even steps the tile's own range, on odd steps the range
+// shifted by the offset of x + c_q (the plane q pulls come from), widened by
+// a few cells for the row-end wraps and rounded out to 16 bytes.  The ranges
+// lie in the population arena: every plane is followed by the next one, and
+// the arena's guard bands exceed the largest shift.
+template <int PREC, int ODD, bool SINGLE>
+__device__ __forceinline__ void prefetch_tile(const SweepArgs &a, int tile, int tcells) {
+    const int q = (int)threadIdx.x;
+    if (q >= Q || tile >= a.ntiles) return;
+    const int li = tile_lattice<SINGLE>(a, tile);
+    const LatDev &L = SINGLE ? a.lat0 : a.lat[li];
+    const long long start = (long long)(tile - L.tile0) * tcells;
+    const long long cnt = min((long long)tcells, (long long)L.n - start);
+    if (cnt <= 0) return;
+    constexpr int EB = (int)sizeof(typename Store<PREC>::T);
+    const long long e0 = L.f_off + (long long)q * L.npad + start + (ODD ? L.off[q] : 0) - 8;
+    const uintptr_t b0 = (reinterpret_cast<uintptr_t>(a.f) + (uintptr_t)(e0 * EB)) & ~(uintptr_t)15;
+    const uintptr_t b1 = (reinterpret_cast<uintptr_t>(a.f) + (uintptr_t)((e0 + cnt + 16) * EB) + 15) & ~(uintptr_t)15;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(b0), "r"((uint32_t)(b1 - b0)) : "memory");
 }
 
 // Per-thread partial sums of force and torque.  FP64 lattices keep them in
@@ -769,6 +870,7 @@ __global__ void __launch_bounds__(256, SweepBounds<PREC>::MINB)
     tkey[threadIdx.x] = SLOT_EMPTY;
 
     for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+        if (a.pf_ahead) prefetch_tile<PREC, ODD, SINGLE>(a, tile + a.pf_ahead, (int)blockDim.x);
         const int li = tile_lattice<SINGLE>(a, tile);
         const LatDev &L = SINGLE ? a.lat0 : a.lat[li];
         const int idx = (tile - L.tile0) * blockDim.x + threadIdx.x;
@@ -923,6 +1025,37 @@ template <int PREC, int V> struct Pack {
         else
             return __hiloint2double((int)w[2 * k + 1], (int)w[2 * k]);
     }
+    // elements k, k+1 (k even) as a pair in the compute precision (FP32 and
+    // the 16-bit forms)
+    __device__ __forceinline__ float2 get2(int k) const {
+        if constexpr (PREC == LBM_F16_OFFSET) {
+            return __half22float2(*reinterpret_cast<const __half2 *>(&w[k >> 1]));
+        } else if constexpr (PREC == LBM_BF16_OFFSET) {
+            const uint32_t x = w[k >> 1];
+            return make_float2(__uint_as_float(x << 16), __uint_as_float(x & 0xffff0000u));
+        } else {
+            return make_float2(__uint_as_float(w[k]), __uint_as_float(w[k + 1]));
+        }
+    }
+    // elements k, k+1 <- v (r0, r1: rounding bits of the BF16 form; `plain`:
+    // no NaN among the two values, so the BF16 form rounds by integer adds)
+    __device__ __forceinline__ void set2(int k, float2 v, uint32_t r0, uint32_t r1, bool plain) {
+        if constexpr (PREC == LBM_F16_OFFSET) {
+            const __half2 h = __float22half2_rn(v);
+            w[k >> 1] = *reinterpret_cast<const uint32_t *>(&h);
+        } else if constexpr (PREC == LBM_BF16_OFFSET) {
+            if (plain) {
+                // bf16_bits_sr of each value: add the rounding bits below the
+                // kept 16 bits, keep the upper halves of both words
+                w[k >> 1] = __byte_perm(__float_as_uint(v.x) + r0, __float_as_uint(v.y) + r1, 0x7632);
+            } else {
+                w[k >> 1] = (uint32_t)bf16_bits_sr(v.x, r0) | ((uint32_t)bf16_bits_sr(v.y, r1) << 16);
+            }
+        } else {
+            w[k] = __float_as_uint(v.x);
+            w[k + 1] = __float_as_uint(v.y);
+        }
+    }
     // element k <- v in the storage form (r16: rounding bits of the BF16 form)
     __device__ __forceinline__ void set(int k, C v, uint32_t r16) {
         if constexpr (EB == 2) {
@@ -957,14 +1090,14 @@ __device__ __forceinline__ int x_off(const CellGeom &c, const LatDev &L, int q, 
     return 0;
 }
 
-// A group with a wall, obstacle or near-obstacle cell: its cells one at a
-// time through the one-cell paths, each loading its own populations again
-// (from L1/L2: the group's loads brought them in).  Out of line, so that the
-// packed group is dead at this call and the bulk path keeps its registers.
+// A group with a wall, obstacle or near-obstacle cell: its bulk and wall
+// cells one at a time through the one-cell paths (each loading its own
+// populations), its near-obstacle cells left to the warp's near pass (bit k
+// of the result: cell idx0 + k).
 template <int PREC, int ODD, int V>
-__device__ __noinline__ void group_mixed(const SweepArgs &a, const LatDev &L, int li, int idx0, uint32_t fl,
-                                         uint32_t seed, uint32_t *tkey, typename Acc<PREC>::V *tval) {
-    using C = typename Store<PREC>::C;
+__device__ __forceinline__ uint32_t group_mixed(const SweepArgs &a, const LatDev &L, int li, int idx0, uint32_t fl,
+                                             uint32_t seed, uint32_t *tkey, typename Acc<PREC>::V *tval) {
+    uint32_t deferred = 0;
 #pragma unroll 1
     for (int k = 0; k < V; ++k) {
         const int idx = idx0 + k;
@@ -977,13 +1110,43 @@ __device__ __noinline__ void group_mixed(const SweepArgs &a, const LatDev &L, in
             else
                 wall_cell<PREC, ODD, 1>(a, L, li, idx, tkey, tval, seed);
         } else if (f & F_NEAR) {
-            if (a.near_list) continue;  // split sweep: the near kernel updates it
-            C g[Q];
-            near_cell<PREC, ODD, 0>(a, L, li, idx, tkey, tval, nullptr, g, seed);
+            if (!a.near_list) deferred |= 1u << k;  // split sweep: the near kernel updates it
         } else {
             bulk_cell<PREC, ODD>(a, L, idx, seed);
         }
     }
+    return deferred;
+}
+
+// The warp's near-obstacle cells, one per lane: the deferred cells of all
+// lanes (bit k of `deferred`: cell idx0 + k of this lane's group) are listed
+// in the warp's slice of shared memory in lane order and taken 32 at a time.
+// A near cell's update touches only its own slots (AA), so doing it after the
+// bulk cells of its warp changes nothing but the order of independent writes;
+// run cell by cell inside the groups, the long near path would be issued up
+// to V times per warp.  Called by the whole warp.
+template <int PREC, int ODD, int V>
+__device__ __forceinline__ void near_pass(const SweepArgs &a, const LatDev &L, int li, int idx0, uint32_t deferred,
+                                       int *list, uint32_t seed, uint32_t *tkey, typename Acc<PREC>::V *tval) {
+    using C = typename Store<PREC>::C;
+    const int lane = threadIdx.x & 31;
+    const int cnt = __popc(deferred);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    int w = incl - cnt;
+    for (uint32_t m = deferred; m; m &= m - 1) list[w++] = idx0 + __ffs(m) - 1;
+    __syncwarp();
+#pragma unroll 1
+    for (int j = lane; j < total; j += 32) {
+        C g[Q];
+        near_cell<PREC, ODD, 0>(a, L, li, list[j], tkey, tval, nullptr, g, seed);
+    }
+    __syncwarp();
 }
 
 // Loads of a group at the bulk pull addresses (odd steps: plane opp(q) at
@@ -1044,9 +1207,9 @@ __device__ __forceinline__ void group_store(const LatDev &L, typename Store<PREC
 // A group of V cells of the fluid row next to a moving wall layer (every cell
 // flagged F_YLO, SIDE 0, or F_YHI, SIDE 1): the wall path of wall_cell on the
 // packed group -- the same loads, arithmetic, rounding bits and per-cell
-// momentum hand-over.  Out of line: the bulk path keeps its registers.
+// momentum hand-over.
 template <int PREC, int ODD, int V, int SIDE>
-__device__ __noinline__ void group_wall(const SweepArgs &a, const LatDev &L, int li, int idx0, uint32_t seed,
+__device__ __forceinline__ void group_wall(const SweepArgs &a, const LatDev &L, int li, int idx0, uint32_t seed,
                                         uint32_t *tkey, typename Acc<PREC>::V *tval) {
     CellGeom cg;
     if (ODD) cg = cell_geom(L, idx0);
@@ -1094,60 +1257,75 @@ __device__ __noinline__ void group_wall(const SweepArgs &a, const LatDev &L, int
     group_store<PREC, ODD, V, SIDE>(L, base, np, idx0, cg, pk);
 }
 
-// One group: all bulk fluid (packed collision, vector accesses), a wall-row
-// group, all solid, or else cell by cell.
+// The groups of a warp that are not plain bulk fluid on aligned rows (`mine`:
+// this lane's group is one; fl: its flag bytes): a wall-row group (every cell
+// F_YLO, or every cell F_YHI) on the packed wall path, any other group cell
+// by cell, and then the warp's near-obstacle cells one per lane.  Out of line
+// and called once per warp after the packed groups, so the bulk path has no
+// call site to keep registers across and its packed values stay in
+// registers.  Called by the whole warp.
 template <int PREC, int ODD, int V>
-__device__ __forceinline__ void group_cells(const SweepArgs &a, const LatDev &L, int li, int idx0, bool bulk_tile,
-                                            bool vec, uint32_t seed, uint32_t *tkey, typename Acc<PREC>::V *tval) {
+__device__ __noinline__ void group_slow(const SweepArgs &a, const LatDev &L, int li, int idx0, bool mine, bool vec,
+                                        uint32_t fl, int *list, uint32_t seed, uint32_t *tkey,
+                                        typename Acc<PREC>::V *tval) {
+    constexpr uint32_t REP = V == 2 ? 0x0101u : 0x01010101u;
+    uint32_t deferred = 0;
+    if (mine) {
+        const uint32_t f0 = fl & 0xFFu;
+        if (vec && fl == REP * f0 && f0 == (F_NEAR | F_YLO))
+            group_wall<PREC, ODD, V, 0>(a, L, li, idx0, seed, tkey, tval);
+        else if (vec && fl == REP * f0 && f0 == (F_NEAR | F_YHI))
+            group_wall<PREC, ODD, V, 1>(a, L, li, idx0, seed, tkey, tval);
+        else
+            deferred = group_mixed<PREC, ODD, V>(a, L, li, idx0, fl, seed, tkey, tval);
+    }
+    if (__any_sync(0xffffffffu, deferred != 0)) near_pass<PREC, ODD, V>(a, L, li, idx0, deferred, list, seed, tkey, tval);
+}
+
+// One group of bulk fluid cells on an aligned row: packed collision, vector
+// accesses.
+template <int PREC, int ODD, int V>
+__device__ __forceinline__ void group_bulk(const SweepArgs &a, const LatDev &L, int idx0, uint32_t seed) {
     using S = Store<PREC>;
     using T = typename S::T;
     using C = typename S::C;
     using Pk = Pack<PREC, V>;
-    constexpr uint32_t REP = V == 2 ? 0x0101u : 0x01010101u;
-    // flag bytes of the V cells (byte k: cell idx0 + k); the flag planes are
-    // padded to whole tiles of 256 cells with zeros, so the load stays inside
-    uint32_t fl = 0;
-    if (!bulk_tile) {
-        const uint8_t *fp = a.flags + L.c_off + idx0;
-        if constexpr (V == 2)
-            fl = *reinterpret_cast<const unsigned short *>(fp);
-        else
-            fl = *reinterpret_cast<const unsigned int *>(fp);
-    }
-    // vector accesses need a whole group of one row (nx a multiple of V); the
-    // ragged last group and lattices with other nx go cell by cell
-    if (!vec) {
-        group_mixed<PREC, ODD, V>(a, L, li, idx0, fl, seed, tkey, tval);
-        return;
-    }
-    if (fl != 0) {
-        if ((fl & (REP * F_SOLID)) == REP * F_SOLID) return;  // wall or obstacle cells only
-        const uint32_t f0 = fl & 0xFFu;
-        if (fl == REP * f0 && f0 == (F_NEAR | F_YLO)) {
-            group_wall<PREC, ODD, V, 0>(a, L, li, idx0, seed, tkey, tval);
-        } else if (fl == REP * f0 && f0 == (F_NEAR | F_YHI)) {
-            group_wall<PREC, ODD, V, 1>(a, L, li, idx0, seed, tkey, tval);
-        } else {
-            group_mixed<PREC, ODD, V>(a, L, li, idx0, fl, seed, tkey, tval);
-        }
-        return;
-    }
     T *base = reinterpret_cast<T *>(a.f) + L.f_off;
     const long long np = L.npad;
     CellGeom cg;
     if (ODD) cg = cell_geom(L, idx0);
     Pk pk[Q];
     group_load<PREC, ODD, V, -1>(L, base, np, idx0, cg, pk);
-    // every cell of the group is bulk fluid
+    if constexpr (PREC == LBM_F64) {
 #pragma unroll
-    for (int k = 0; k < V; ++k) {
-        C g[Q];
+        for (int k = 0; k < V; ++k) {
+            C g[Q];
 #pragma unroll
-        for (int q = 0; q < Q; ++q) g[q] = pk[q].get(k);
-        collide_lat<C>(g, L);
-        Rnd<PREC> rnd(seed, L.c_off + idx0 + k);
+            for (int q = 0; q < Q; ++q) g[q] = pk[q].get(k);
+            collide_lat<C>(g, L);
 #pragma unroll
-        for (int q = 0; q < Q; ++q) pk[q].set(k, g[q], rnd.next());
+            for (int q = 0; q < Q; ++q) pk[q].set(k, g[q], 0u);
+        }
+    } else {
+        // two cells per paired instruction
+#pragma unroll
+        for (int k = 0; k < V; k += 2) {
+            float2 g[Q];
+#pragma unroll
+            for (int q = 0; q < Q; ++q) g[q] = pk[q].get2(k);
+            collide2_lat(g, L);
+            // a NaN among the outputs needs a NaN or infinite moment: with
+            // the equilibrium base of both cells finite the BF16 form rounds
+            // every value by integer adds
+            const float b0 = g[0].x, b1 = g[0].y;
+            const bool plain = PREC != LBM_BF16_OFFSET || (isfinite(b0) && isfinite(b1));
+            Rnd<PREC> r0(seed, L.c_off + idx0 + k), r1(seed, L.c_off + idx0 + k + 1);
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const uint32_t a0 = r0.next(), a1 = r1.next();
+                pk[q].set2(k, g[q], a0, a1, plain);
+            }
+        }
     }
     group_store<PREC, ODD, V, -1>(L, base, np, idx0, cg, pk);
 }
@@ -1164,16 +1342,42 @@ __global__ void __launch_bounds__((GroupBounds<PREC, V>::MAXT), (GroupBounds<PRE
     const uint32_t seed = PREC == LBM_BF16_OFFSET ? step_seed(a.tick) : 0u;
     __shared__ uint32_t tkey[256];
     __shared__ typename Acc<PREC>::V tval[256][6];
+    __shared__ int nlist[GroupBounds<PREC, V>::MAXT / 32][32 * V];  // per warp: its deferred near cells
     tkey[threadIdx.x] = SLOT_EMPTY;
+    constexpr uint32_t REP = V == 2 ? 0x0101u : 0x01010101u;
     const int tcells = V * (int)blockDim.x;
     for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+        if (a.pf_ahead) prefetch_tile<PREC, ODD, SINGLE>(a, tile + a.pf_ahead, tcells);
+        // uniform per block: a tile lies in one lattice
         const int li = tile_lattice<SINGLE>(a, tile);
         const LatDev &L = SINGLE ? a.lat0 : a.lat[li];
         const int idx0 = (tile - L.tile0) * tcells + V * (int)threadIdx.x;
-        if (idx0 >= L.n) continue;
         const bool bulk_tile = a.tbits && !((a.tbits[tile >> 5] >> (tile & 31)) & 1u);
-        const bool vec = idx0 + V <= L.n && (L.nx & (V - 1)) == 0;
-        group_cells<PREC, ODD, V>(a, L, li, idx0, bulk_tile, vec, seed, &tkey[threadIdx.x], tval[threadIdx.x]);
+        // vector accesses need a whole group: on even steps (a cell's own
+        // slots) any group but the ragged last one, on odd steps a group of
+        // one row (nx a multiple of V); the others go cell by cell
+        const bool vec = idx0 + V <= L.n && (!ODD || (L.nx & (V - 1)) == 0);
+        // flag bytes of the V cells (byte k: cell idx0 + k); the flag planes
+        // are padded to whole tiles of 256 cells with zeros, so the load
+        // stays inside
+        uint32_t fl = 0;
+        if (!bulk_tile && idx0 < L.n) {
+            const uint8_t *fp = a.flags + L.c_off + idx0;
+            if constexpr (V == 2)
+                fl = *reinterpret_cast<const unsigned short *>(fp);
+            else
+                fl = *reinterpret_cast<const unsigned int *>(fp);
+        }
+        bool slow = false;
+        if (idx0 < L.n) {
+            if (vec && fl == 0)
+                group_bulk<PREC, ODD, V>(a, L, idx0, seed);
+            else
+                slow = (fl & (REP * F_SOLID)) != REP * F_SOLID || !vec;  // not wall or obstacle cells only
+        }
+        if (__any_sync(0xffffffffu, slow))
+            group_slow<PREC, ODD, V>(a, L, li, idx0, slow, vec, fl, nlist[threadIdx.x >> 5], seed,
+                                     &tkey[threadIdx.x], tval[threadIdx.x]);
     }
     flush_forces<PREC>(a, tkey, tval);
 }
@@ -1506,42 +1710,88 @@ __global__ void __launch_bounds__(256, SweepBounds<PREC>::MINB)
 }
 
 // Split sweep, step 1: the near-obstacle cells (F_NEAR without a flat-wall
-// flag) of the tiles marked in the tile bits, compacted into a.near_list --
-// one block per tile (blockDim = cells per tile), one atomic per tile.
+// flag) of the tiles marked in the tile bits, compacted into a.near_list.
+// Each warp takes a contiguous range of tpw tiles: it counts its cells, a
+// lane reading eight flag bytes with one load, reserves its slice of the
+// list with one atomic and writes the cells in tile and cell order (lane l
+// holds cells 8l .. 8l+7 of each 256 of the tile), so neighbouring list
+// entries are neighbouring cells.  One atomic per warp with cells rather
+// than per tile (same-address atomics serialise), no barrier, and every
+// load of a warp independent of the warp's other loads.
+__device__ __forceinline__ bool near_listed(uint8_t fl) { return (fl & F_NEAR) && !(fl & (F_YLO | F_YHI)); }
+
+// Bit b of the result: cell c + b of the tile is listed (c a multiple of 8;
+// bytes at or beyond the lattice's last cell count as empty).
+__device__ __forceinline__ uint32_t near_bits8(const uint8_t *fp, int c, int valid) {
+    if (c >= valid) return 0u;
+    const uint2 w = *reinterpret_cast<const uint2 *>(fp + c);
+    uint32_t m = 0;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const uint8_t fl = (uint8_t)((b < 4 ? w.x : w.y) >> (8 * (b & 3)));
+        if (c + b < valid && near_listed(fl)) m |= 1u << b;
+    }
+    return m;
+}
+
 template <bool SINGLE>
-__global__ void __launch_bounds__(1024) near_list_kernel(const __grid_constant__ SweepArgs a) {
+__global__ void __launch_bounds__(256) near_list_kernel(const __grid_constant__ SweepArgs a, int tcells, int tpw) {
     pdl_enter();
-    const int tile = blockIdx.x;
-    if (a.tbits && !((a.tbits[tile >> 5] >> (tile & 31)) & 1u)) return;  // uniform per block
-    const int li = tile_lattice<SINGLE>(a, tile);
-    const LatDev &L = SINGLE ? a.lat0 : a.lat[li];
-    const int idx = (tile - L.tile0) * blockDim.x + threadIdx.x;
-    bool nearc = false;
-    if (idx < L.n) {
-        const uint8_t fl = a.flags[L.c_off + idx];
-        nearc = (fl & F_NEAR) && !(fl & (F_YLO | F_YHI));
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int t0 = warp * tpw, t1 = min(a.ntiles, t0 + tpw);
+    uint32_t n = 0;  // this lane's cells
+    for (int tile = t0; tile < t1; ++tile) {
+        if (a.tbits && !((a.tbits[tile >> 5] >> (tile & 31)) & 1u)) continue;  // uniform per warp
+        const LatDev &L = SINGLE ? a.lat0 : a.lat[tile_lattice<SINGLE>(a, tile)];
+        const int s0 = (tile - L.tile0) * tcells;
+        const uint8_t *fp = a.flags + L.c_off + s0;
+        const int valid = min(tcells, L.n - s0);
+        for (int c = 8 * lane; c < tcells; c += 256) n += (uint32_t)__popc(near_bits8(fp, c, valid));
     }
-    __shared__ uint32_t wcount[32];
-    __shared__ uint32_t base;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t bal = __ballot_sync(0xffffffffu, nearc);
-    if (lane == 0) wcount[warp] = (uint32_t)__popc(bal);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t sum = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            const uint32_t c = wcount[w];
-            wcount[w] = sum;
-            sum += c;
+    // inclusive prefix of the lanes' counts
+    uint32_t incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const uint32_t total = __shfl_sync(FULL, incl, 31);
+    if (total == 0) return;  // the whole warp
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(a.near_count, total);
+    base = __shfl_sync(FULL, base, 0);
+    // second walk: per tile (and per 256 cells of it) the lanes' counts again,
+    // written from the warp's running offset in cell order
+    for (int tile = t0; tile < t1; ++tile) {
+        if (a.tbits && !((a.tbits[tile >> 5] >> (tile & 31)) & 1u)) continue;
+        const LatDev &L = SINGLE ? a.lat0 : a.lat[tile_lattice<SINGLE>(a, tile)];
+        const int s0 = (tile - L.tile0) * tcells;
+        const uint8_t *fp = a.flags + L.c_off + s0;
+        const int valid = min(tcells, L.n - s0);
+        for (int cb = 0; cb < tcells; cb += 256) {
+            const int c = cb + 8 * lane;
+            uint32_t m = c < tcells ? near_bits8(fp, c, valid) : 0u;
+            const uint32_t cnt = (uint32_t)__popc(m);
+            uint32_t x = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t v = __shfl_up_sync(FULL, x, o);
+                if (lane >= o) x += v;
+            }
+            uint32_t pos = base + x - cnt;
+            for (; m; m &= m - 1) a.near_list[pos++] = (uint32_t)(L.c_off + s0 + c + __ffs(m) - 1);
+            base += __shfl_sync(FULL, x, 31);
         }
-        base = sum ? atomicAdd(a.near_count, sum) : 0u;
     }
-    __syncthreads();
-    if (nearc) a.near_list[base + wcount[warp] + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)(L.c_off + idx);
 }
 
 // Split sweep, step 3: one thread per listed near-obstacle cell (a
-// persistent grid over the list), the same update as the fused path.
+// persistent grid over the list), the same update as the fused path.  (A
+// contiguous slice of the list per warp, which would let a thread's partial
+// sums run over cells of one body, measured slower on GB300 than the grid
+// stride, whose concurrent warps work on neighbouring list entries.)
 template <int PREC, int ODD, bool SINGLE>
 __global__ void __launch_bounds__(256, SweepBounds<PREC>::MINB) near_kernel(const __grid_constant__ SweepArgs a) {
     pdl_enter();
@@ -1638,8 +1888,12 @@ cudaError_t launch_one(int variant, const SweepArgs &a, int grid, int block, int
             nwave = wave[dev];
         }
         e = cudaMemsetAsync(a.near_count, 0, sizeof(uint32_t), s);
-        // one list block per tile, one thread per cell of the tile
-        if (e == cudaSuccess) e = launch_pdl(near_list_kernel<SINGLE>, a.ntiles, block * cpt, 0, s, a);
+        // tiles per list warp: about 48 warps per SM over all tiles
+        const int tcells = block * cpt;
+        const int want = nwave * 4;
+        const int tpw = a.ntiles > want ? (a.ntiles + want - 1) / want : 1;
+        const int lwarps = (a.ntiles + tpw - 1) / tpw;
+        if (e == cudaSuccess) e = launch_pdl(near_list_kernel<SINGLE>, (lwarps + 7) / 8, 256, 0, s, a, tcells, tpw);
         if (e == cudaSuccess) e = launch_direct<PREC, ODD, SINGLE>(a, grid, block, cpt, s);
         if (e == cudaSuccess) e = launch_pdl(near_kernel<PREC, ODD, SINGLE>, nwave, 128, 0, s, a);
         return e;

@@ -55,7 +55,7 @@ class lbm_info(C.Structure):
                 ("device_bytes", C.c_size_t), ("sweep_grid", C.c_int), ("sweep_block", C.c_int),
                 ("bytes_per_population", C.c_int), ("sweep_split", C.c_int),
                 ("remap_fused", C.c_int), ("remap_grid", C.c_int),
-                ("cells_per_thread", C.c_int), ("device", C.c_int)]
+                ("cells_per_thread", C.c_int), ("device", C.c_int), ("sweep_prefetch", C.c_int)]
 
 
 # name -> (restype, argtypes) for every entry point of include/lbm.h
@@ -83,6 +83,7 @@ SIGNATURES = {
     "lbm_set_graphs": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_set_wait_limit": (C.c_int, [C.c_void_p, C.c_uint]),
     "lbm_set_sweep_split": (C.c_int, [C.c_void_p, C.c_int]),
+    "lbm_set_sweep_prefetch": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_set_remap_fused": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_set_momentum_stabilisation": (C.c_int, [C.c_void_p, C.c_int]),
     "lbm_set_sweep_timing": (C.c_int, [C.c_void_p, C.c_int]),
@@ -248,6 +249,10 @@ def lbm_autotune(ctx):
 
 def lbm_set_sweep_split(ctx, enable: bool):
     _check(load().lbm_set_sweep_split(ctx, 1 if enable else 0), ctx)
+
+
+def lbm_set_sweep_prefetch(ctx, enable: bool):
+    _check(load().lbm_set_sweep_prefetch(ctx, 1 if enable else 0), ctx)
 
 
 def lbm_set_remap_fused(ctx, enable: bool):

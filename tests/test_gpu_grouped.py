@@ -172,3 +172,32 @@ def test_cells_per_thread_argument_errors(lbm):
             lbm.lbm_set_cells_per_thread(g.h, bad)
     lbm.lbm_set_cells_per_thread(g.h, 2)
     g.close()
+
+
+@pytest.mark.parametrize("cpt", [1, 2, 4])
+@pytest.mark.parametrize("grid", [0, 40])
+def test_l2_prefetch_changes_nothing(lbm, cpt, grid):
+    """The direct sweep's L2 prefetch is a hint: populations and flags
+    bit-identical with and without it, forces to the rounding of the FP64
+    atomics' order (one tile per block, where a block prefetches the tile one
+    wave ahead, and a persistent grid, where it prefetches its own next tile).
+    The body is fixed, so the forces do not feed back into the fields."""
+    lat = shear_lattice(64, 30, 26, 0.75, 0.015)
+    rng = SplitMix64(41)
+    ps = [Particle(pos=(30.0, 14.5, 12.5), quat=quat_from_axis(rng.unit_vector()), semi_axes=(7.0, 2.5, 2.5),
+                   fixed=1)]
+    out = []
+    for pf in (False, True):
+        g = lbm.Simulation(lat, ps, prec="f32")
+        lbm.lbm_set_launch(g.h, 128, grid)
+        lbm.lbm_set_cells_per_thread(g.h, cpt)
+        lbm.lbm_set_sweep_prefetch(g.h, pf)
+        assert (lbm.lbm_get_info(g.h).sweep_prefetch > 0) == pf
+        g.step(9)
+        _, _, fl, _, d = g.fields()
+        F, M = g.forces()
+        out.append((fl, d, F, M))
+        g.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    for a, b in zip(out[0][2:], out[1][2:]):
+        assert np.allclose(a, b, rtol=1e-9, atol=1e-12)
