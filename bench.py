@@ -42,8 +42,10 @@ SWEEP_SOURCES = ("paper_1503_06869_gb300/csrc/lbm_sweep.cuh", "paper_1503_06869_
                  "paper_1503_06869_gb300/csrc/lbm_sweep_f32.cu", "paper_1503_06869_gb300/csrc/lbm_sweep_f16.cu",
                  "paper_1503_06869_gb300/csrc/lbm_sweep_bf16.cu", "paper_1503_06869_gb300/csrc/lbm_internal.cuh")
 SWEEP_TRAFFIC = {
-    ("shear256x128x128_spheroid24x3x3", "f32"): {"bytes": 570.72e6, "src": "3e5fec48d2252c95",
-                                                "profile": "profiles/sweep_kernel_shear256x128x128_f32.md"},
+    ("shear256x128x128_spheroid24x3x3", "f32"): {"bytes": 571.19e6, "src": "fa5a4500a6e8ecbc",
+                                                "profile": "profiles/sweep_group_shear256x128x128_f32.md"},
+    ("shear256x128x128_spheroid24x3x3", "f16"): {"bytes": 262.47e6, "src": "fa5a4500a6e8ecbc",
+                                                "profile": "profiles/sweep_group_shear256x128x128_f16.md"},
 }
 
 
@@ -355,6 +357,8 @@ def measure(args, w, prec, world, local, launch=None, cpt=None, closure_params=N
         lbm.lbm_set_launch(h, launch, 0)
         if cpt:
             lbm.lbm_set_cells_per_thread(h, cpt)
+        if getattr(args, "split", False):
+            lbm.lbm_set_sweep_split(h, True)
     info = lbm.lbm_get_info(h)
     sim.step(args.warmup)
     sim.sync()
@@ -502,6 +506,8 @@ def main():
                     help="fixed sweep block size (0 ring, -1 staged, 32..256 direct) instead of the autotuner's "
                          "choice; for profiling runs, where the profiler's serialisation skews the autotuner")
     ap.add_argument("--cpt", type=int, default=None, help="with --launch: cells per thread of the direct sweep")
+    ap.add_argument("--split", action="store_true",
+                    help="with --launch: near-obstacle cells in a kernel of their own (split sweep)")
     ap.add_argument("--remap-fused", action="store_true",
                     help="run the re-mapping step as one cooperative launch instead of five launches")
     args = ap.parse_args()

@@ -292,10 +292,12 @@ lbm_status lbm_set_launch(lbm_ctx *ctx, int block, int grid);
  * values of one population plane for its cells with one vector access
  * wherever they are contiguous and aligned (every plane on even steps; on odd
  * steps the planes of directions without an x component, when nx is a
- * multiple of the group size); a direct-sweep tile then covers block * cpt
- * cells.  Results are identical for every setting.  Default 1; the autotuner
- * chooses.  Takes effect at the next lbm_step.  Errors: LBM_ERR_ARG for any
- * other value. */
+ * multiple of the group size), and the FP32 / FP16 / BF16 sweeps collide two
+ * cells at once on paired FP32 instructions; a direct-sweep tile then covers
+ * block * cpt cells.  Results agree to rounding for every setting (the same
+ * arithmetic, contracted into fused multiply-adds differently).  Default 1;
+ * the autotuner chooses.  Takes effect at the next lbm_step.  Errors:
+ * LBM_ERR_ARG for any other value. */
 lbm_status lbm_set_cells_per_thread(lbm_ctx *ctx, int cpt);
 
 /* Split direct sweep (enable != 0): near-obstacle cells (those next to a
