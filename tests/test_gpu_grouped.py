@@ -189,8 +189,8 @@ def test_l2_prefetch_changes_nothing(lbm, cpt, grid):
     out = []
     for pf in (False, True):
         g = lbm.Simulation(lat, ps, prec="f32")
-        lbm.lbm_set_launch(g.h, 128, grid)
         lbm.lbm_set_cells_per_thread(g.h, cpt)
+        lbm.lbm_set_launch(g.h, 128, grid)  # after the tile size is set
         lbm.lbm_set_sweep_prefetch(g.h, pf)
         assert (lbm.lbm_get_info(g.h).sweep_prefetch > 0) == pf
         g.step(9)
