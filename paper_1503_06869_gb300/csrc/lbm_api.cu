@@ -857,7 +857,9 @@ lbm_status lbm_set_particles(lbm_ctx *ctx, const lbm_particle *p, int n) {
         density[i] = b.density;
     }
     // re-mapping launch shape: about four box cells per thread for the
-    // largest body, at most ~64 blocks per SM over all bodies
+    // largest body, at most ~16 blocks per SM over all bodies (with many
+    // small bodies a block per body: each block first loads its body's
+    // record, a cost paid once per block)
     {
         double amax = 0.0;
         for (int i = 0; i < n; ++i)
@@ -869,7 +871,7 @@ lbm_status lbm_set_particles(lbm_ctx *ctx, const lbm_particle *p, int n) {
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const long long cap = (long long)(sms > 0 ? sms : 1) * 64;
+        const long long cap = (long long)(sms > 0 ? sms : 1) * 16;
         if (n > 0 && bpb * n > cap) bpb = cap / n > 0 ? cap / n : 1;
         ctx->remap_bpb = (int)bpb;
         ctx->np_pending = n;
