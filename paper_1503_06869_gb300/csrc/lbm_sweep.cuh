@@ -1204,6 +1204,27 @@ __device__ __forceinline__ void group_store(const LatDev &L, typename Store<PREC
     }
 }
 
+// The same stores for the cells of the group in `keep` only (bit k: cell
+// idx0 + k), element by element where a cell is left out.
+template <int PREC, int ODD, int V>
+__device__ __forceinline__ void group_store_masked(const LatDev &L, typename Store<PREC>::T *base, long long np,
+                                                   int idx0, const CellGeom &cg, const Pack<PREC, V> (&pk)[Q],
+                                                   uint32_t keep) {
+    constexpr uint32_t ALL = (1u << V) - 1u;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        typename Store<PREC>::T *row =
+            !ODD ? base + opp(q) * np + idx0 : base + q * np + idx0 + yz_off(cg, q);
+        if (keep == ALL && (!ODD || cx(q) == 0)) {
+            pk[q].vstore(row);
+        } else {
+#pragma unroll
+            for (int k = 0; k < V; ++k)
+                if ((keep >> k) & 1u) pk[q].estore(row + k + (ODD ? x_off<V>(cg, L, q, k) : 0), k);
+        }
+    }
+}
+
 // A group of V cells of the fluid row next to a moving wall layer (every cell
 // flagged F_YLO, SIDE 0, or F_YHI, SIDE 1): the wall path of wall_cell on the
 // packed group -- the same loads, arithmetic, rounding bits and per-cell
@@ -1282,10 +1303,21 @@ __device__ __noinline__ void group_slow(const SweepArgs &a, const LatDev &L, int
     if (__any_sync(0xffffffffu, deferred != 0)) near_pass<PREC, ODD, V>(a, L, li, idx0, deferred, list, seed, tkey, tval);
 }
 
-// One group of bulk fluid cells on an aligned row: packed collision, vector
-// accesses.
-template <int PREC, int ODD, int V>
-__device__ __forceinline__ void group_bulk(const SweepArgs &a, const LatDev &L, int idx0, uint32_t seed) {
+// One group on an aligned row whose cells in `keep` (bit k: cell idx0 + k)
+// are bulk fluid: packed collision, vector accesses, stores for the kept
+// cells only (MASKED; without it every cell is stored).  keep is every cell
+// but in the split sweep, where a group may
+// also hold near-obstacle cells (the near kernel updates them) or obstacle
+// cells: the packed path then runs for the whole group and stores only the
+// bulk cells.  A bulk cell has no obstacle neighbour, so its loads and
+// arithmetic are those of an all-bulk group; the other cells' values are read
+// and discarded (a cell's update writes exactly the slots it reads, so the
+// near kernel still finds the near cells' slots untouched).  In dense
+// suspensions most warps hold such a group, and this keeps them off the
+// one-cell slow path.
+template <int PREC, int ODD, int V, bool MASKED>
+__device__ __forceinline__ void group_bulk(const SweepArgs &a, const LatDev &L, int idx0, uint32_t seed,
+                                           uint32_t keep) {
     using S = Store<PREC>;
     using T = typename S::T;
     using C = typename S::C;
@@ -1327,7 +1359,10 @@ __device__ __forceinline__ void group_bulk(const SweepArgs &a, const LatDev &L, 
             }
         }
     }
-    group_store<PREC, ODD, V, -1>(L, base, np, idx0, cg, pk);
+    if constexpr (MASKED)
+        group_store_masked<PREC, ODD, V>(L, base, np, idx0, cg, pk, keep);
+    else
+        group_store<PREC, ODD, V, -1>(L, base, np, idx0, cg, pk);
 }
 
 // Resident blocks of 256 threads per SM for the grouped sweep: 2 leaves 128
@@ -1335,7 +1370,9 @@ __device__ __forceinline__ void group_bulk(const SweepArgs &a, const LatDev &L, 
 // loads in flight per SM partition against 24 for the one-cell sweep.
 template <int PREC, int V> struct GroupBounds { static constexpr int MAXT = 256, MINB = 2; };
 
-template <int PREC, int ODD, bool SINGLE, int V>
+// SPLIT: the split sweep (near-obstacle cells left to the near kernel), a
+// template parameter so that the other sweeps' code stays as it is.
+template <int PREC, int ODD, bool SINGLE, int V, bool SPLIT>
 __global__ void __launch_bounds__((GroupBounds<PREC, V>::MAXT), (GroupBounds<PREC, V>::MINB))
     sweep_group(const __grid_constant__ SweepArgs a) {
     pdl_enter();
@@ -1370,10 +1407,29 @@ __global__ void __launch_bounds__((GroupBounds<PREC, V>::MAXT), (GroupBounds<PRE
         }
         bool slow = false;
         if (idx0 < L.n) {
-            if (vec && fl == 0)
-                group_bulk<PREC, ODD, V>(a, L, idx0, seed);
-            else
-                slow = (fl & (REP * F_SOLID)) != REP * F_SOLID || !vec;  // not wall or obstacle cells only
+            if constexpr (SPLIT) {
+                // the packed path stores the bulk cells of a group whose other
+                // cells are near-obstacle or obstacle cells (a wall-row cell
+                // sends the group to the slow path)
+                uint32_t keep = 0;
+                bool other = false;
+#pragma unroll
+                for (int k = 0; k < V; ++k) {
+                    const uint32_t f = (fl >> (8 * k)) & 0xFFu;
+                    if (f == 0) keep |= 1u << k;
+                    else if (!(f & F_SOLID) && (f & (F_YLO | F_YHI))) other = true;
+                }
+                if (vec && !other) {
+                    if (keep) group_bulk<PREC, ODD, V, true>(a, L, idx0, seed, keep);
+                } else {
+                    slow = (fl & (REP * F_SOLID)) != REP * F_SOLID || !vec;
+                }
+            } else {
+                if (vec && fl == 0)
+                    group_bulk<PREC, ODD, V, false>(a, L, idx0, seed, (1u << V) - 1u);
+                else
+                    slow = (fl & (REP * F_SOLID)) != REP * F_SOLID || !vec;  // not wall or obstacle cells only
+            }
         }
         if (__any_sync(0xffffffffu, slow))
             group_slow<PREC, ODD, V>(a, L, li, idx0, slow, vec, fl, nlist[threadIdx.x >> 5], seed,
@@ -1848,9 +1904,14 @@ cudaError_t raise_smem_once(K kernel, int smem, bool (&done)[LAUNCH_MAX_DEVICES]
 
 template <int PREC, int ODD, bool SINGLE>
 cudaError_t launch_direct(const SweepArgs &a, int grid, int block, int cpt, cudaStream_t s) {
-    if (cpt == 2) return launch_pdl(sweep_group<PREC, ODD, SINGLE, 2>, grid, block, 0, s, a);
+    const bool split = a.near_list != nullptr;
+    if (cpt == 2)
+        return split ? launch_pdl(sweep_group<PREC, ODD, SINGLE, 2, true>, grid, block, 0, s, a)
+                     : launch_pdl(sweep_group<PREC, ODD, SINGLE, 2, false>, grid, block, 0, s, a);
     if constexpr (PREC != LBM_F64) {
-        if (cpt == 4) return launch_pdl(sweep_group<PREC, ODD, SINGLE, 4>, grid, block, 0, s, a);
+        if (cpt == 4)
+            return split ? launch_pdl(sweep_group<PREC, ODD, SINGLE, 4, true>, grid, block, 0, s, a)
+                         : launch_pdl(sweep_group<PREC, ODD, SINGLE, 4, false>, grid, block, 0, s, a);
     }
     if (cpt != 1) return cudaErrorInvalidValue;
     return launch_pdl(sweep_kernel<PREC, ODD, SINGLE>, grid, block, 0, s, a);
@@ -1928,10 +1989,10 @@ int sweep_max_blocks_prec(int variant, int block, int cpt) {
         cudaFuncSetAttribute(sweep_ring<PREC, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_ring<PREC, 1, false>, RingCfg<PREC>::TILE, smem);
     } else if (cpt == 2) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_group<PREC, 1, false, 2>, block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_group<PREC, 1, false, 2, false>, block, 0);
     } else if (cpt == 4) {
         if constexpr (PREC != LBM_F64)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_group<PREC, 1, false, 4>, block, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_group<PREC, 1, false, 4, false>, block, 0);
     } else {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<PREC, 1, false>, block, 0);
     }
