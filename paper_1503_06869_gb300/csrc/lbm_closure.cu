@@ -68,6 +68,33 @@ __device__ __forceinline__ void tile_mma(float (&c)[4], const SMat &A, int m0, c
     }
 }
 
+// The same product when A is row-major (a[r][k] at A + r lda + k) and B is
+// stored as its transpose, B(k, n) at Bt + n ldb + k (a layer's weights
+// [out][in]): the fragments come straight from shared memory with ldmatrix
+// (four 8x8 matrices of A, two of B per 16-wide k step; lane l gives the
+// address of row l % 8 of matrix l / 8), whose register layout is the
+// m16n8k16 fragment layout.  Rows must start on 16 bytes (lda, ldb multiples
+// of 8 halves, 16-byte aligned bases).
+__device__ __forceinline__ void tile_mma_ldm(float (&c)[4], const __half *A, int lda, int m0, const __half *Bt,
+                                             int ldb, int n0, int K) {
+    const int lane = threadIdx.x & 31;
+    const int mat = lane >> 3, row = lane & 7;
+    // A: matrices (rows 0-7, k 0-7), (rows 8-15, k 0-7), (rows 0-7, k 8-15), (rows 8-15, k 8-15)
+    const __half *pa = A + (m0 + row + 8 * (mat & 1)) * lda + 8 * (mat >> 1);
+    // B: matrices (n 0-7, k 0-7), (n 0-7, k 8-15); lanes 16-31 repeat lanes 0-15
+    const __half *pb = Bt + (n0 + row) * ldb + 8 * (mat & 1);
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        uint32_t a[4], b[2];
+        asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                     : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3])
+                     : "r"((uint32_t)__cvta_generic_to_shared(pa + k0)));
+        asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];"
+                     : "=r"(b[0]), "=r"(b[1])
+                     : "r"((uint32_t)__cvta_generic_to_shared(pb + k0)));
+        mma16816(c, a, b);
+    }
+}
+
 // Shared-memory image of the network: FP16 weights zero-padded to the tile
 // grid ([out][in] rows, W1 to 96 inputs, W4 to 16 outputs), FP32 biases.
 struct NetSmem {
@@ -100,18 +127,15 @@ template <bool RELU>
 __device__ __forceinline__ void dense(const __half *in, int ldin, int K, const __half *w, int ldw,
                                       const float *bias, int N, __half *out, int ldout, int m0) {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const SMat A{in, ldin, false}, B{w, ldw, true};
     for (int n0 = 0; n0 < N; n0 += 8) {
         float c[4] = {0.f, 0.f, 0.f, 0.f};
-        tile_mma(c, A, m0, B, n0, K);
+        tile_mma_ldm(c, in, ldin, m0, w, ldw, n0, K);
         const int col = n0 + 2 * t;
         float v[4] = {c[0] + bias[col], c[1] + bias[col + 1], c[2] + bias[col], c[3] + bias[col + 1]};
         if (RELU)
             for (int k = 0; k < 4; ++k) v[k] = fmaxf(v[k], 0.f);
-        out[(m0 + g) * ldout + col] = __float2half(v[0]);
-        out[(m0 + g) * ldout + col + 1] = __float2half(v[1]);
-        out[(m0 + g + 8) * ldout + col] = __float2half(v[2]);
-        out[(m0 + g + 8) * ldout + col + 1] = __float2half(v[3]);
+        *reinterpret_cast<__half2 *>(out + (m0 + g) * ldout + col) = __floats2half2_rn(v[0], v[1]);
+        *reinterpret_cast<__half2 *>(out + (m0 + g + 8) * ldout + col) = __floats2half2_rn(v[2], v[3]);
     }
 }
 
@@ -128,7 +152,7 @@ __device__ __forceinline__ void forward_rows(const NetSmem &s, const __half *X, 
     __syncwarp();
     const int t = threadIdx.x & 3;
     c[0] = c[1] = c[2] = c[3] = 0.f;
-    tile_mma(c, SMat{h3, NH, false}, m0, SMat{s.w4, NH, true}, 0, NH);
+    tile_mma_ldm(c, h3, NH, m0, s.w4, NH, 0, NH);
     c[0] += s.b4[2 * t];
     c[1] += s.b4[2 * t + 1];
     c[2] += s.b4[2 * t];
@@ -275,6 +299,9 @@ struct InferSmem {
     __half x[ROWS * NINP];
     __half h1[ROWS * NH], h2[ROWS * NH], h3[ROWS * NH];
 };
+// ldmatrix reads rows of 16 bytes: every array starts on 16 bytes
+static_assert(sizeof(NetSmem) % 16 == 0 && (ROWS * NINP * 2) % 16 == 0 && (ROWS * NH * 2) % 16 == 0,
+              "16-byte aligned shared-memory operands");
 
 // Block of 8 warps, 128 rows.  APPLY: rows are bodies; their outputs become
 // the world-frame correction R dF * mu*gamma*a*b, R dM * mu*gamma*a^2*b, added
