@@ -998,6 +998,13 @@ template <int PREC, int V> struct Pack {
         else
             __stcs(reinterpret_cast<uint2 *>(p), make_uint2(w[2 * k], w[2 * k + 1]));
     }
+    // elements 1 and 2 (V = 4) to p, p[0] and p[1] (an aligned pair)
+    __device__ __forceinline__ void pstore12(T *p) const {
+        if constexpr (EB == 2)
+            __stcs(reinterpret_cast<unsigned int *>(p), __byte_perm(w[0], w[1], 0x5432));
+        else if constexpr (EB == 4)
+            __stcs(reinterpret_cast<uint2 *>(p), make_uint2(w[1], w[2]));
+    }
     // the group shifted by one element: elements 1..V-1 of own then element 0
     // of nbr (up: nbr is the group at x + V), or element V-1 of nbr then
     // elements 0..V-2 of own (nbr is the group at x - V)
@@ -1198,8 +1205,16 @@ __device__ __forceinline__ void group_store(const LatDev &L, typename Store<PREC
             pk[q].vstore(base + q * np + idx0 + yz_off(cg, q));
         } else {
             typename Store<PREC>::T *row = base + q * np + idx0 + yz_off(cg, q);
+            if constexpr (V == 4 && sizeof(typename Store<PREC>::T) <= 4) {
+                // elements 1 and 2 land on an aligned pair inside the row
+                // (x0 + 2, x0 + 3 going +x; x0, x0 + 1 going -x): one store
+                pk[q].estore(row + x_off<V>(cg, L, q, 0), 0);
+                pk[q].pstore12(row + (cx(q) > 0 ? 2 : 0));
+                pk[q].estore(row + 3 + x_off<V>(cg, L, q, 3), 3);
+            } else {
 #pragma unroll
-            for (int k = 0; k < V; ++k) pk[q].estore(row + k + x_off<V>(cg, L, q, k), k);
+                for (int k = 0; k < V; ++k) pk[q].estore(row + k + x_off<V>(cg, L, q, k), k);
+            }
         }
     }
 }
