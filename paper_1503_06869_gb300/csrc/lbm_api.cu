@@ -386,7 +386,7 @@ lbm_status enqueue_step(lbm_ctx *ctx, bool timed) {
         ctx->launches += sweep_kernels(ctx) + 1;
         if (ctx->np > 0) {
             CK(launch_remap_step(ctx->prec, 1 - parity, ra, ctx->remap_bpb, ctx->stream));
-            ctx->launches += kernels_per_remap_step();
+            ctx->launches += kernels_per_remap_step(ctx->np);
         }
     }
     ctx->t += 1;

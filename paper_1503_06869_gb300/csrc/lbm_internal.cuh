@@ -501,6 +501,6 @@ cudaError_t launch_set_pdfs(int prec, int next_parity, const LatDev &h, const La
 cudaError_t launch_links(const LatDev &h, const LatDev *d, const uint8_t *flags,
                          const uint32_t *pid, int *block_counts, int nblocks, int32_t *idx,
                          int8_t *q, uint32_t *pid_out, int cap, int *total, cudaStream_t s);
-int kernels_per_remap_step();
+int kernels_per_remap_step(int np);
 
 }  // namespace lbm

@@ -562,7 +562,21 @@ __device__ void remap_region(const RemapArgs &a, int unit, int bpb) {
         RegionCell c;
         box_cell(reg, L, r0, r1, r2, c);
         const long long cg = L.c_off + c.idx;
-        if (PASS == 0) {  // uncover
+        if (PASS == 2) {  // a single body: uncover and claim in one pass
+            const uint32_t cur = a.pid[cg];
+            if (cur == (uint32_t)p) {
+                if (!inside_fast(L, pos, R64, semi, bf, c.i, c.j, c.k)) {
+                    a.pid[cg] = PID_FLUID;
+                    a.pid_prev[cg] = (uint32_t)p;
+                    P.changed[p] = 1;
+                    return mark_changed(a.flags, cg) ? cg : -1;
+                }
+            } else if (cur == PID_FLUID && inside_fast(L, pos, R64, semi, bf, c.i, c.j, c.k)) {
+                a.pid[cg] = (uint32_t)p;
+                P.changed[p] = 1;
+                return mark_changed(a.flags, cg) ? cg : -1;
+            }
+        } else if (PASS == 0) {  // uncover
             if (a.pid[cg] == (uint32_t)p && !inside_fast(L, pos, R64, semi, bf, c.i, c.j, c.k)) {
                 a.pid[cg] = PID_FLUID;
                 a.pid_prev[cg] = (uint32_t)p;
@@ -1286,8 +1300,15 @@ __global__ void link_write_kernel(const LatDev *lat, const uint8_t *flags, const
 template <int PREC>
 cudaError_t remap_step_prec(int next_parity, const RemapArgs &a, int bpb, cudaStream_t s) {
     const unsigned grid = (unsigned)bpb * (unsigned)a.P.np;
-    cudaError_t e = launch_pdl(remap_region_kernel<0>, grid, REMAP_BLOCK, 0, s, a, bpb);
-    if (e == cudaSuccess) e = launch_pdl(remap_region_kernel<1>, grid, REMAP_BLOCK, 0, s, a, bpb);
+    cudaError_t e;
+    if (a.P.np == 1) {
+        // one body: no cell can pass from one body to another, so uncover and
+        // claim need no pass between them
+        e = launch_pdl(remap_region_kernel<2>, grid, REMAP_BLOCK, 0, s, a, bpb);
+    } else {
+        e = launch_pdl(remap_region_kernel<0>, grid, REMAP_BLOCK, 0, s, a, bpb);
+        if (e == cudaSuccess) e = launch_pdl(remap_region_kernel<1>, grid, REMAP_BLOCK, 0, s, a, bpb);
+    }
     // the list passes: each thread strides over the list (its length is known
     // on the device only); the changed cells scale with the bodies, so the
     // grid is the region passes' (one box's blocks per body), at most about
@@ -1359,7 +1380,7 @@ cudaError_t set_pdfs_prec(int next_parity, const LatDev &h, const LatDev *d, voi
 
 }  // namespace
 
-int kernels_per_remap_step() { return 4; }
+int kernels_per_remap_step(int np) { return np == 1 ? 3 : 4; }
 
 int remap_fused_max_blocks() {
     int dev = 0, sms = 0, coop = 0, nb = 0;

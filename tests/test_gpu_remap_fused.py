@@ -92,7 +92,9 @@ def test_fused_matches_separate_many_bodies_eager(lbm):
 
 
 def test_fused_launch_count(lbm):
-    """One launch per re-mapping step in place of five."""
+    """One launch per re-mapping step in place of the rigid-body update and
+    the re-mapping passes (uncover and claim in one pass for a single body,
+    then fix-up and flags: four launches)."""
     w = small_shear(seed=3, n=32)
     counts = {}
     for fused in (True, False):
@@ -103,4 +105,5 @@ def test_fused_launch_count(lbm):
         s.step(10)
         counts[fused] = lbm.lbm_get_launch_count(s.h) - n0
         s.close()
-    assert counts[False] - counts[True] == 10 * 4
+    assert len(w.particles) == 1
+    assert counts[False] - counts[True] == 10 * 3
