@@ -361,6 +361,7 @@ def measure(args, w, prec, world, local, launch=None, cpt=None, closure_params=N
             lbm.lbm_set_cells_per_thread(h, cpt)
         if getattr(args, "split", False):
             lbm.lbm_set_sweep_split(h, True)
+        lbm.lbm_set_sweep_prefetch(h, ["off", "all", "even", "odd"].index(getattr(args, "prefetch", "off")))
     info = lbm.lbm_get_info(h)
     sim.step(args.warmup)
     sim.sync()
@@ -399,7 +400,8 @@ def measure(args, w, prec, world, local, launch=None, cpt=None, closure_params=N
                         "step_achieved": round(step_achieved, 1), "step_frac": round(step_achieved / peak, 4),
                         "peak_kind": f"{peak_kind} hbm_gbs"},
            "launch": {"block": info.sweep_block, "grid": info.sweep_grid, "cells_per_thread": info.cells_per_thread,
-                      "split": bool(info.sweep_split), "remap_fused": bool(info.remap_fused)}}
+                      "split": bool(info.sweep_split), "remap_fused": bool(info.remap_fused),
+                      "l2_prefetch": ["off", "all", "even steps", "odd steps"][info.sweep_prefetch_mode]}}
     if e2e_steps:
         # every step: H2D of the particles' external loads from pinned memory,
         # the step, D2H of the hydrodynamic force/torque (synchronising)
@@ -510,6 +512,9 @@ def main():
     ap.add_argument("--cpt", type=int, default=None, help="with --launch: cells per thread of the direct sweep")
     ap.add_argument("--split", action="store_true",
                     help="with --launch: near-obstacle cells in a kernel of their own (split sweep)")
+    ap.add_argument("--prefetch", default="off", choices=["off", "all", "even", "odd"],
+                    help="with --launch: L2 prefetch of a later tile in every sweep, or in the even- or odd-step "
+                         "sweeps only")
     ap.add_argument("--remap-fused", action="store_true",
                     help="run the re-mapping step as one cooperative launch instead of five launches")
     args = ap.parse_args()

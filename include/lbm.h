@@ -270,6 +270,7 @@ typedef struct lbm_info {
     int cells_per_thread;       /* direct sweep: consecutive cells per thread (1, 2, 4) */
     int device;                 /* CUDA device of the context */
     int sweep_prefetch;         /* tiles ahead that the direct sweep prefetches into L2 (0: none) */
+    int sweep_prefetch_mode;    /* LBM_PREFETCH_* in effect (LBM_PREFETCH_OFF outside the direct sweep) */
 } lbm_info;
 
 lbm_status lbm_get_info(lbm_ctx *ctx, lbm_info *info);
@@ -309,15 +310,24 @@ lbm_status lbm_set_cells_per_thread(lbm_ctx *ctx, int cpt);
  * takes effect at the next lbm_step. */
 lbm_status lbm_set_sweep_split(lbm_ctx *ctx, int enable);
 
-/* L2 prefetch in the direct sweep (enable != 0; default 0): a block that
- * starts a tile first asks the L2 for the population ranges of a later tile
- * (the tile one resident wave ahead, or the block's own next tile on a
- * persistent grid) with one asynchronous bulk prefetch per population plane,
- * so that tile's loads find their data in the L2.  A hint only: results do
- * not change.  Chosen per context by lbm_autotune; takes effect at the next
- * lbm_step.  No counterpart in the paper (a launch parameter like the block
- * size). */
-lbm_status lbm_set_sweep_prefetch(lbm_ctx *ctx, int enable);
+/* L2 prefetch in the direct sweep: a block that starts a tile first asks the
+ * L2 for the population ranges of a later tile (the tile one resident wave
+ * ahead, or the block's own next tile on a persistent grid) with one
+ * asynchronous bulk prefetch per population plane, so that tile's loads find
+ * their data in the L2.  mode: LBM_PREFETCH_OFF (0, the default),
+ * LBM_PREFETCH_ALL (1: every sweep), LBM_PREFETCH_EVEN (2: only the sweeps of
+ * even time steps, which read and write each cell's own slots) or
+ * LBM_PREFETCH_ODD (3: only the sweeps of odd time steps, which read and
+ * write the neighbours' slots); the two kinds of sweep gain or lose from it
+ * differently.  Any other mode: LBM_ERR_ARG.  A hint only: results do not
+ * change.  Chosen per context by lbm_autotune (for each parity on its own);
+ * takes effect at the next lbm_step.  No counterpart in the paper (a launch
+ * parameter like the block size). */
+#define LBM_PREFETCH_OFF 0
+#define LBM_PREFETCH_ALL 1
+#define LBM_PREFETCH_EVEN 2
+#define LBM_PREFETCH_ODD 3
+lbm_status lbm_set_sweep_prefetch(lbm_ctx *ctx, int mode);
 
 /* Fused re-mapping step (enable != 0; default 0): the rigid-body update
  * (Sec. 4.3) and the four passes of the obstacle re-mapping (Sec. 4.2:

@@ -47,7 +47,7 @@ struct lbm_ctx {
     uint32_t *chg = nullptr;        // re-mapping: cells whose owner changed this step
     uint32_t *chg_n = nullptr;
     bool split = false;             // direct sweep: near-obstacle cells in a kernel of their own
-    bool prefetch = false;          // direct sweep: L2 prefetch of a later tile
+    int prefetch = 0;               // direct sweep: L2 prefetch of a later tile, bit p: sweeps of parity p
     __half *cl_par = nullptr;       // learned closure: FP16 network parameters
     bool closure = false;
     uint32_t *err = nullptr;
@@ -250,7 +250,9 @@ SweepArgs sweep_args(lbm_ctx *ctx) {
     a.nbody = ctx->nbody;
     a.tick = ctx->tick;
     const bool split = ctx->split && ctx->variant == SWEEP_DIRECT;
-    a.pf_ahead = ctx->variant == SWEEP_DIRECT && ctx->prefetch ? prefetch_ahead(ctx) : 0;
+    const int ahead = ctx->variant == SWEEP_DIRECT && ctx->prefetch ? prefetch_ahead(ctx) : 0;
+    a.pf_ahead[0] = (ctx->prefetch & 1) ? ahead : 0;
+    a.pf_ahead[1] = (ctx->prefetch & 2) ? ahead : 0;
     a.near_list = split ? ctx->near_list : nullptr;
     a.near_count = split ? ctx->near_count : nullptr;
     return a;
@@ -1270,6 +1272,11 @@ lbm_status lbm_get_info(lbm_ctx *ctx, lbm_info *info) {
     info->cells_per_thread = ctx->variant == SWEEP_DIRECT ? ctx->cpt : 1;
     info->device = ctx->device;
     info->sweep_prefetch = ctx->variant == SWEEP_DIRECT && ctx->prefetch ? prefetch_ahead(ctx) : 0;
+    info->sweep_prefetch_mode = ctx->variant != SWEEP_DIRECT ? LBM_PREFETCH_OFF
+                                : ctx->prefetch == 3         ? LBM_PREFETCH_ALL
+                                : ctx->prefetch == 1         ? LBM_PREFETCH_EVEN
+                                : ctx->prefetch == 2         ? LBM_PREFETCH_ODD
+                                                             : LBM_PREFETCH_OFF;
     return LBM_OK;
 }
 
@@ -1324,65 +1331,75 @@ lbm_status lbm_autotune(lbm_ctx *ctx, int *block_out, int *grid_out) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     // candidates: the ring sweep (block 0), the staged sweep (block -1) and
     // the direct sweep at two block sizes with 1, 2 or 4 cells per thread,
-    // fused or split, with and without L2 prefetch, each with persistent
-    // grids (1x, 2x resident) and one tile per block
+    // fused or split, each with persistent grids (1x, 2x resident) and one
+    // tile per block; the direct sweep's L2 prefetch is chosen for the even-
+    // and the odd-step sweeps on their own (each timed with and without it)
     struct Cand {
         int block, cpt;
-        bool split, prefetch;
+        bool split;
     };
-    std::vector<Cand> cands = {{0, 1, false, false}, {-1, 1, false, false}};
+    std::vector<Cand> cands = {{0, 1, false}, {-1, 1, false}};
     for (int blk : {128, 256})
         for (int c : {1, 2, 4})
             if (sweep_cpt_supported(ctx->prec, c))
-                for (bool sp : {false, true})
-                    for (bool pf : {false, true}) cands.push_back({blk, c, sp, pf});
+                for (bool sp : {false, true}) cands.push_back({blk, c, sp});
     double best = 1e30;
     int bb = ctx->variant == SWEEP_RING ? 0 : (ctx->variant == SWEEP_STAGED ? -1 : ctx->block);
     int bg = ctx->grid, bc = ctx->cpt;
-    bool bsplit = ctx->split, bpf = ctx->prefetch;
-    cudaEvent_t e0, e1;
-    CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
+    bool bsplit = ctx->split;
+    int bpf = ctx->prefetch;
+    constexpr int REPS = 4;
+    cudaEvent_t ev[2 * REPS + 1];
+    for (cudaEvent_t &e : ev) CK(cudaEventCreate(&e));
     for (const Cand &cand : cands) {
         ctx->cpt = cand.cpt;
         lbm_status s = lbm_set_launch(ctx, cand.block, 0);
         if (s != LBM_OK) break;
         ctx->split = cand.split;
-        ctx->prefetch = cand.prefetch;
         const int occ = sweep_max_active_blocks(ctx->prec, ctx->variant, ctx->block, ctx->cpt);
         if (occ <= 0) continue;
         const int grids[] = {sms * occ, 2 * sms * occ, ctx->ntiles};
         for (int gr : grids) {
             if (gr > ctx->ntiles) gr = ctx->ntiles;
             ctx->grid = gr;
-            SweepArgs sa = sweep_args(ctx);
-            for (int w = 0; w < 2; ++w) {
-                CK(launch_sweep(ctx->prec, 0, ctx->variant, sa, gr, ctx->block, ctx->cpt, ctx->stream));
-                CK(launch_sweep(ctx->prec, 1, ctx->variant, sa, gr, ctx->block, ctx->cpt, ctx->stream));
+            // ms[pf][parity]: summed over REPS sweeps of that parity
+            float ms[2][2] = {{0.f, 0.f}, {1e30f, 1e30f}};
+            for (int pf = 0; pf < (ctx->variant == SWEEP_DIRECT ? 2 : 1); ++pf) {
+                ctx->prefetch = pf ? 3 : 0;
+                SweepArgs sa = sweep_args(ctx);
+                for (int w = 0; w < 2; ++w) {
+                    CK(launch_sweep(ctx->prec, 0, ctx->variant, sa, gr, ctx->block, ctx->cpt, ctx->stream));
+                    CK(launch_sweep(ctx->prec, 1, ctx->variant, sa, gr, ctx->block, ctx->cpt, ctx->stream));
+                }
+                CK(cudaEventRecord(ev[0], ctx->stream));
+                for (int r = 0; r < REPS; ++r) {
+                    CK(launch_sweep(ctx->prec, 0, ctx->variant, sa, gr, ctx->block, ctx->cpt, ctx->stream));
+                    CK(cudaEventRecord(ev[2 * r + 1], ctx->stream));
+                    CK(launch_sweep(ctx->prec, 1, ctx->variant, sa, gr, ctx->block, ctx->cpt, ctx->stream));
+                    CK(cudaEventRecord(ev[2 * r + 2], ctx->stream));
+                }
+                CK(cudaEventSynchronize(ev[2 * REPS]));
+                ctx->launches += 2 * (2 + REPS) * sweep_kernels(ctx);
+                ms[pf][0] = ms[pf][1] = 0.f;
+                for (int k = 0; k < 2 * REPS; ++k) {
+                    float t = 0.f;
+                    CK(cudaEventElapsedTime(&t, ev[k], ev[k + 1]));
+                    ms[pf][k & 1] += t;
+                }
             }
-            CK(cudaEventRecord(e0, ctx->stream));
-            const int reps = 4;
-            for (int r = 0; r < reps; ++r) {
-                CK(launch_sweep(ctx->prec, 0, ctx->variant, sa, gr, ctx->block, ctx->cpt, ctx->stream));
-                CK(launch_sweep(ctx->prec, 1, ctx->variant, sa, gr, ctx->block, ctx->cpt, ctx->stream));
-            }
-            CK(cudaEventRecord(e1, ctx->stream));
-            CK(cudaEventSynchronize(e1));
-            ctx->launches += 2 * (2 + reps) * sweep_kernels(ctx);
-            float ms = 0.f;
-            CK(cudaEventElapsedTime(&ms, e0, e1));
-            if (ms < best) {
-                best = ms;
+            const int pe = ms[1][0] < ms[0][0] ? 1 : 0, po = ms[1][1] < ms[0][1] ? 1 : 0;
+            const double total = (double)ms[pe][0] + ms[po][1];
+            if (total < best) {
+                best = total;
                 bb = cand.block;
                 bg = gr;
                 bc = cand.cpt;
                 bsplit = ctx->split;
-                bpf = ctx->prefetch;
+                bpf = pe | (po << 1);
             }
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    for (cudaEvent_t &e : ev) cudaEventDestroy(e);
     ctx->split = bsplit;
     ctx->prefetch = bpf;
     ctx->cpt = bb > 0 ? bc : 1;
@@ -1406,11 +1423,13 @@ lbm_status lbm_set_sweep_split(lbm_ctx *ctx, int enable) {
     return LBM_OK;
 }
 
-lbm_status lbm_set_sweep_prefetch(lbm_ctx *ctx, int enable) {
+lbm_status lbm_set_sweep_prefetch(lbm_ctx *ctx, int mode) {
     if (!ctx) return LBM_ERR_ARG;
+    if (mode < LBM_PREFETCH_OFF || mode > LBM_PREFETCH_ODD)
+        return fail(ctx, LBM_ERR_ARG, "prefetch mode must be one of LBM_PREFETCH_OFF/ALL/EVEN/ODD");
     DevGuard dg(ctx);
     CK(cudaStreamSynchronize(ctx->stream));
-    ctx->prefetch = enable != 0;
+    ctx->prefetch = mode == LBM_PREFETCH_ALL ? 3 : mode == LBM_PREFETCH_EVEN ? 1 : mode == LBM_PREFETCH_ODD ? 2 : 0;
     drop_graph(ctx);
     return LBM_OK;
 }

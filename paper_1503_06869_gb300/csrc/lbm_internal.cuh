@@ -185,8 +185,9 @@ struct SweepArgs {
     const int *tile_lat;     // batches: lattice of every tile (null: binary search on tile0)
     const uint32_t *tick;    // step counter (seed of the BF16 stochastic rounding)
     // direct sweep: a block starting tile t asks the L2 to fetch the
-    // population ranges of tile t + pf_ahead (0: no prefetch)
-    int pf_ahead;
+    // population ranges of tile t + pf_ahead[parity] (0: no prefetch), per
+    // step parity (index 0: even-step sweeps, 1: odd)
+    int pf_ahead[2];
 };
 
 // Stochastic rounding of the BF16 sweep stores.  A bfloat16 keeps 8

@@ -870,7 +870,7 @@ __global__ void __launch_bounds__(256, SweepBounds<PREC>::MINB)
     tkey[threadIdx.x] = SLOT_EMPTY;
 
     for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-        if (a.pf_ahead) prefetch_tile<PREC, ODD, SINGLE>(a, tile + a.pf_ahead, (int)blockDim.x);
+        if (a.pf_ahead[ODD]) prefetch_tile<PREC, ODD, SINGLE>(a, tile + a.pf_ahead[ODD], (int)blockDim.x);
         const int li = tile_lattice<SINGLE>(a, tile);
         const LatDev &L = SINGLE ? a.lat0 : a.lat[li];
         const int idx = (tile - L.tile0) * blockDim.x + threadIdx.x;
@@ -1240,6 +1240,56 @@ __device__ __forceinline__ void group_store_masked(const LatDev &L, typename Sto
     }
 }
 
+// Neighbour offsets of each cell of a group on its own (odd steps of a
+// lattice whose nx is not a multiple of V, where a group may end a row or
+// straddle two): element k of plane q sits at idx0 + k + nb_off(cell k, q).
+template <int V> struct GroupGeom {
+    CellGeom c[V];
+};
+
+template <int V>
+__device__ __forceinline__ void group_geom(const LatDev &L, int idx0, GroupGeom<V> &gg) {
+#pragma unroll
+    for (int k = 0; k < V; ++k) gg.c[k] = cell_geom(L, idx0 + k);
+}
+
+// Odd-step loads of such a group, element by element (the rest direction
+// from the cells' own slots, aligned).
+template <int PREC, int V>
+__device__ __forceinline__ void group_load_el(typename Store<PREC>::T *base, long long np, int idx0,
+                                              const GroupGeom<V> &gg, Pack<PREC, V> (&pk)[Q]) {
+    pk[0].vload(base + idx0);
+#pragma unroll
+    for (int q = 1; q < Q; ++q) {
+        const int p = opp(q);  // read plane opp(q) at x - c_q = x + c_p
+        const typename Store<PREC>::T *plane = base + p * np + idx0;
+#pragma unroll
+        for (int k = 0; k < V; ++k) pk[q].eload(plane + k + nb_off(gg.c[k], p), k);
+    }
+}
+
+// Odd-step stores of such a group (slot q of x + c_q), the cells in `keep`.
+template <int PREC, int V>
+__device__ __forceinline__ void group_store_el(typename Store<PREC>::T *base, long long np, int idx0,
+                                               const GroupGeom<V> &gg, const Pack<PREC, V> (&pk)[Q],
+                                               uint32_t keep) {
+    constexpr uint32_t ALL = (1u << V) - 1u;
+    if (keep == ALL) {
+        pk[0].vstore(base + idx0);
+    } else {
+#pragma unroll
+        for (int k = 0; k < V; ++k)
+            if ((keep >> k) & 1u) pk[0].estore(base + idx0 + k, k);
+    }
+#pragma unroll
+    for (int q = 1; q < Q; ++q) {
+        typename Store<PREC>::T *plane = base + q * np + idx0;
+#pragma unroll
+        for (int k = 0; k < V; ++k)
+            if ((keep >> k) & 1u) pk[q].estore(plane + k + nb_off(gg.c[k], q), k);
+    }
+}
+
 // A group of V cells of the fluid row next to a moving wall layer (every cell
 // flagged F_YLO, SIDE 0, or F_YHI, SIDE 1): the wall path of wall_cell on the
 // packed group -- the same loads, arithmetic, rounding bits and per-cell
@@ -1330,7 +1380,7 @@ __device__ __noinline__ void group_slow(const SweepArgs &a, const LatDev &L, int
 // near kernel still finds the near cells' slots untouched).  In dense
 // suspensions most warps hold such a group, and this keeps them off the
 // one-cell slow path.
-template <int PREC, int ODD, int V, bool MASKED>
+template <int PREC, int ODD, int V, bool MASKED, bool AL = true>
 __device__ __forceinline__ void group_bulk(const SweepArgs &a, const LatDev &L, int idx0, uint32_t seed,
                                            uint32_t keep) {
     using S = Store<PREC>;
@@ -1339,10 +1389,16 @@ __device__ __forceinline__ void group_bulk(const SweepArgs &a, const LatDev &L, 
     using Pk = Pack<PREC, V>;
     T *base = reinterpret_cast<T *>(a.f) + L.f_off;
     const long long np = L.npad;
+    constexpr bool EL = ODD && !AL;  // element accesses at each cell's own offsets
     CellGeom cg;
-    if (ODD) cg = cell_geom(L, idx0);
+    GroupGeom<V> gg;
+    if (ODD && !EL) cg = cell_geom(L, idx0);
+    if (EL) group_geom<V>(L, idx0, gg);
     Pk pk[Q];
-    group_load<PREC, ODD, V, -1>(L, base, np, idx0, cg, pk);
+    if constexpr (EL)
+        group_load_el<PREC, V>(base, np, idx0, gg, pk);
+    else
+        group_load<PREC, ODD, V, -1>(L, base, np, idx0, cg, pk);
     if constexpr (PREC == LBM_F64) {
 #pragma unroll
         for (int k = 0; k < V; ++k) {
@@ -1374,7 +1430,15 @@ __device__ __forceinline__ void group_bulk(const SweepArgs &a, const LatDev &L, 
             }
         }
     }
-    if constexpr (MASKED)
+    if constexpr (EL) {
+        // the offsets again rather than held across the collision (an opaque
+        // copy of idx0 keeps the compiler from reusing the first ones)
+        int i0;
+        asm volatile("mov.b32 %0, %1;" : "=r"(i0) : "r"(idx0));
+        group_geom<V>(L, i0, gg);
+        group_store_el<PREC, V>(base, np, idx0, gg, pk, MASKED ? keep : (1u << V) - 1u);
+    }
+    else if constexpr (MASKED)
         group_store_masked<PREC, ODD, V>(L, base, np, idx0, cg, pk, keep);
     else
         group_store<PREC, ODD, V, -1>(L, base, np, idx0, cg, pk);
@@ -1399,7 +1463,7 @@ __global__ void __launch_bounds__((GroupBounds<PREC, V>::MAXT), (GroupBounds<PRE
     constexpr uint32_t REP = V == 2 ? 0x0101u : 0x01010101u;
     const int tcells = V * (int)blockDim.x;
     for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-        if (a.pf_ahead) prefetch_tile<PREC, ODD, SINGLE>(a, tile + a.pf_ahead, tcells);
+        if (a.pf_ahead[ODD]) prefetch_tile<PREC, ODD, SINGLE>(a, tile + a.pf_ahead[ODD], tcells);
         // uniform per block: a tile lies in one lattice
         const int li = tile_lattice<SINGLE>(a, tile);
         const LatDev &L = SINGLE ? a.lat0 : a.lat[li];
@@ -1407,8 +1471,15 @@ __global__ void __launch_bounds__((GroupBounds<PREC, V>::MAXT), (GroupBounds<PRE
         const bool bulk_tile = a.tbits && !((a.tbits[tile >> 5] >> (tile & 31)) & 1u);
         // vector accesses need a whole group: on even steps (a cell's own
         // slots) any group but the ragged last one, on odd steps a group of
-        // one row (nx a multiple of V); the others go cell by cell
-        const bool vec = idx0 + V <= L.n && (!ODD || (L.nx & (V - 1)) == 0);
+        // one row (nx a multiple of V); the others go cell by cell.  In a
+        // batch, a lattice whose nx is not a multiple of V takes the packed
+        // path on odd steps too, with its neighbour slots accessed element
+        // by element at each cell's own offsets (`al` false; uniform per
+        // block): in small lattices nearly every warp holds a group that
+        // ends or straddles a row, and one such group would otherwise send
+        // the warp down the one-cell path
+        const bool al = !ODD || (L.nx & (V - 1)) == 0;
+        const bool vec = idx0 + V <= L.n && (al || !SINGLE);
         // flag bytes of the V cells (byte k: cell idx0 + k); the flag planes
         // are padded to whole tiles of 256 cells with zeros, so the load
         // stays inside
@@ -1435,19 +1506,29 @@ __global__ void __launch_bounds__((GroupBounds<PREC, V>::MAXT), (GroupBounds<PRE
                     else if (!(f & F_SOLID) && (f & (F_YLO | F_YHI))) other = true;
                 }
                 if (vec && !other) {
-                    if (keep) group_bulk<PREC, ODD, V, true>(a, L, idx0, seed, keep);
+                    if (keep) {
+                        if (SINGLE || al)
+                            group_bulk<PREC, ODD, V, true>(a, L, idx0, seed, keep);
+                        else
+                            group_bulk<PREC, ODD, V, true, false>(a, L, idx0, seed, keep);
+                    }
                 } else {
                     slow = (fl & (REP * F_SOLID)) != REP * F_SOLID || !vec;
                 }
             } else {
-                if (vec && fl == 0)
-                    group_bulk<PREC, ODD, V, false>(a, L, idx0, seed, (1u << V) - 1u);
-                else
+                if (vec && fl == 0) {
+                    if (SINGLE || al)
+                        group_bulk<PREC, ODD, V, false>(a, L, idx0, seed, (1u << V) - 1u);
+                    else
+                        group_bulk<PREC, ODD, V, false, false>(a, L, idx0, seed, (1u << V) - 1u);
+                } else {
                     slow = (fl & (REP * F_SOLID)) != REP * F_SOLID || !vec;  // not wall or obstacle cells only
+                }
             }
         }
+        // the packed wall-row path wants aligned rows
         if (__any_sync(0xffffffffu, slow))
-            group_slow<PREC, ODD, V>(a, L, li, idx0, slow, vec, fl, nlist[threadIdx.x >> 5], seed,
+            group_slow<PREC, ODD, V>(a, L, li, idx0, slow, vec && al, fl, nlist[threadIdx.x >> 5], seed,
                                      &tkey[threadIdx.x], tval[threadIdx.x]);
     }
     flush_forces<PREC>(a, tkey, tval);

@@ -55,7 +55,8 @@ class lbm_info(C.Structure):
                 ("device_bytes", C.c_size_t), ("sweep_grid", C.c_int), ("sweep_block", C.c_int),
                 ("bytes_per_population", C.c_int), ("sweep_split", C.c_int),
                 ("remap_fused", C.c_int), ("remap_grid", C.c_int),
-                ("cells_per_thread", C.c_int), ("device", C.c_int), ("sweep_prefetch", C.c_int)]
+                ("cells_per_thread", C.c_int), ("device", C.c_int), ("sweep_prefetch", C.c_int),
+                ("sweep_prefetch_mode", C.c_int)]
 
 
 # name -> (restype, argtypes) for every entry point of include/lbm.h
@@ -251,8 +252,15 @@ def lbm_set_sweep_split(ctx, enable: bool):
     _check(load().lbm_set_sweep_split(ctx, 1 if enable else 0), ctx)
 
 
-def lbm_set_sweep_prefetch(ctx, enable: bool):
-    _check(load().lbm_set_sweep_prefetch(ctx, 1 if enable else 0), ctx)
+# lbm_set_sweep_prefetch modes (include/lbm.h)
+PREFETCH_OFF, PREFETCH_ALL, PREFETCH_EVEN, PREFETCH_ODD = 0, 1, 2, 3
+
+
+def lbm_set_sweep_prefetch(ctx, mode):
+    """mode: one of PREFETCH_OFF/ALL/EVEN/ODD; True / False stand for ALL / OFF."""
+    if isinstance(mode, bool):
+        mode = PREFETCH_ALL if mode else PREFETCH_OFF
+    _check(load().lbm_set_sweep_prefetch(ctx, int(mode)), ctx)
 
 
 def lbm_set_remap_fused(ctx, enable: bool):

@@ -5,8 +5,9 @@ one-cell sweep.
 Lattices are chosen so that every code path of the grouped sweep runs: nx a
 multiple of the group (vector loads and stores, odd-step x neighbours from
 two aligned groups, periodic wrap at the row ends), nx a multiple of 2 but
-not of 4 (aligned for 2 cells, cell by cell for 4), odd nx (cell by cell), a
-ragged last group, walls, near-obstacle groups and split sweeps.
+not of 4 and odd nx (single lattices: cell by cell on odd steps; batches:
+packed with element accesses inside the rows), a ragged last group, walls,
+near-obstacle groups and split sweeps.
 Tolerances as in test_gpu_parity: velocity relative L2 over fluid cells
 1e-12 (FP64), 1e-5 (FP32), 1e-2 (FP16, BF16); flags and particle ids
 bit-exact.
@@ -164,6 +165,44 @@ def test_grouped_ragged_tail_and_batch(lbm):
         g.close()
 
 
+@pytest.mark.parametrize("split", [False, True])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "bf16"])
+def test_grouped_batch_unaligned_rows_equal_one_cell_sweep(lbm, prec, split):
+    """In a batch, the odd steps of a lattice whose nx is not a multiple of
+    the group run the packed path with element accesses for every group
+    strictly inside a row, and cell by cell at the row ends: with fixed
+    bodies (no feedback) the populations must match the one-cell sweep's to
+    rounding, lattice by lattice."""
+    lats = [shear_lattice(23, 14, 11, 0.8, 0.02), shear_lattice(30, 12, 9, 0.7, 0.015),
+            shear_lattice(21, 13, 10, 0.9, 0.01)]
+    ps = [Particle(pos=(11.3, 6.6, 5.2), quat=quat_from_axis((0.6, 0.64, 0.48)), semi_axes=(6.0, 2.5, 2.5),
+                   fixed=1, cell=0),
+          Particle(pos=(14.2, 5.4, 4.1), quat=quat_from_axis((0.0, 0.6, 0.8)), semi_axes=(5.0, 2.0, 2.0),
+                   fixed=1, cell=1),
+          Particle(pos=(9.7, 6.3, 4.8), quat=quat_from_axis((1.0, 0.0, 0.0)), semi_axes=(4.0, 2.2, 2.2),
+                   fixed=1, cell=2)]
+    tol = {"f64": 1e-13, "f32": 1e-6, "f16": 1e-3, "bf16": 1e-2}[prec]
+    w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)[:, None]
+    ref = None
+    for cpt in (1, 2, 4):
+        if prec == "f64" and cpt == 4:
+            continue
+        g = lbm.Simulation(lats, ps, prec=prec)
+        lbm.lbm_set_launch(g.h, 64, 0)
+        lbm.lbm_set_cells_per_thread(g.h, cpt)
+        lbm.lbm_set_sweep_split(g.h, split)
+        g.step(7)
+        out = [g.fields(cell=c)[2::2] for c in range(len(lats))]
+        g.close()
+        if ref is None:
+            ref = out
+            continue
+        for c, ((fl, d), (_, d0)) in enumerate(zip(out, ref)):
+            m = fl == 0
+            e = np.linalg.norm((d - d0)[:, m]) / np.linalg.norm((d0 - w)[:, m])
+            assert e <= tol, f"cells per thread {cpt}, lattice {c}: offsets differ from the one-cell sweep by {e:.2e}"
+
+
 def test_cells_per_thread_argument_errors(lbm):
     lat = shear_lattice(16, 10, 8, 0.8, 0.01)
     g = lbm.Simulation(lat, [], prec="f64")
@@ -178,7 +217,8 @@ def test_cells_per_thread_argument_errors(lbm):
 @pytest.mark.parametrize("grid", [0, 40])
 def test_l2_prefetch_changes_nothing(lbm, cpt, grid):
     """The direct sweep's L2 prefetch is a hint: populations and flags
-    bit-identical with and without it, forces to the rounding of the FP64
+    bit-identical with and without it (in every sweep, or in the even- or the
+    odd-step sweeps only), forces to the rounding of the FP64
     atomics' order (one tile per block, where a block prefetches the tile one
     wave ahead, and a persistent grid, where it prefetches its own next tile).
     The body is fixed, so the forces do not feed back into the fields."""
@@ -187,17 +227,26 @@ def test_l2_prefetch_changes_nothing(lbm, cpt, grid):
     ps = [Particle(pos=(30.0, 14.5, 12.5), quat=quat_from_axis(rng.unit_vector()), semi_axes=(7.0, 2.5, 2.5),
                    fixed=1)]
     out = []
-    for pf in (False, True):
+    modes = (lbm.PREFETCH_OFF, lbm.PREFETCH_ALL, lbm.PREFETCH_EVEN, lbm.PREFETCH_ODD)
+    for mode in modes:
         g = lbm.Simulation(lat, ps, prec="f32")
         lbm.lbm_set_cells_per_thread(g.h, cpt)
         lbm.lbm_set_launch(g.h, 128, grid)  # after the tile size is set
-        lbm.lbm_set_sweep_prefetch(g.h, pf)
-        assert (lbm.lbm_get_info(g.h).sweep_prefetch > 0) == pf
+        lbm.lbm_set_sweep_prefetch(g.h, mode)
+        info = lbm.lbm_get_info(g.h)
+        assert info.sweep_prefetch_mode == mode
+        assert (info.sweep_prefetch > 0) == (mode != lbm.PREFETCH_OFF)
         g.step(9)
         _, _, fl, _, d = g.fields()
         F, M = g.forces()
         out.append((fl, d, F, M))
+        if mode == lbm.PREFETCH_ODD:
+            for bad in (-1, 4):
+                with pytest.raises(lbm.LBMError):
+                    lbm.lbm_set_sweep_prefetch(g.h, bad)
+            assert lbm.lbm_get_info(g.h).sweep_prefetch_mode == mode
         g.close()
-    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
-    for a, b in zip(out[0][2:], out[1][2:]):
-        assert np.allclose(a, b, rtol=1e-9, atol=1e-12)
+    for o in out[1:]:
+        assert np.array_equal(out[0][0], o[0]) and np.array_equal(out[0][1], o[1])
+        for a, b in zip(out[0][2:], o[2:]):
+            assert np.allclose(a, b, rtol=1e-9, atol=1e-12)
