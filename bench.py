@@ -42,12 +42,14 @@ SWEEP_SOURCES = ("paper_1503_06869_gb300/csrc/lbm_sweep.cuh", "paper_1503_06869_
                  "paper_1503_06869_gb300/csrc/lbm_sweep_f32.cu", "paper_1503_06869_gb300/csrc/lbm_sweep_f16.cu",
                  "paper_1503_06869_gb300/csrc/lbm_sweep_bf16.cu", "paper_1503_06869_gb300/csrc/lbm_internal.cuh")
 SWEEP_TRAFFIC = {
-    ("shear256x128x128_spheroid24x3x3", "f32"): {"bytes": 569.83e6, "src": "a5f9851465518991",
+    ("shear256x128x128_spheroid24x3x3", "f32"): {"bytes": 569.97e6, "src": "3a1aa1b81564e284",
                                                 "profile": "profiles/sweep_group_dram_shear256x128x128.md"},
-    ("shear256x128x128_spheroid24x3x3", "f16"): {"bytes": 260.61e6, "src": "a5f9851465518991",
+    ("shear256x128x128_spheroid24x3x3", "f16"): {"bytes": 260.26e6, "src": "3a1aa1b81564e284",
                                                 "profile": "profiles/sweep_group_dram_shear256x128x128.md"},
-    ("shear256x128x128_spheroid24x3x3", "bf16"): {"bytes": 254.58e6, "src": "a5f9851465518991",
+    ("shear256x128x128_spheroid24x3x3", "bf16"): {"bytes": 254.74e6, "src": "3a1aa1b81564e284",
                                                  "profile": "profiles/sweep_group_dram_shear256x128x128.md"},
+    ("batched512_shear_cells", "f32"): {"bytes": 16697.4e6, "src": "3a1aa1b81564e284",
+                                       "profile": "profiles/launches_batched512_f32.md"},
 }
 
 

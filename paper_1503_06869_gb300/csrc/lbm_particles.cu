@@ -730,12 +730,6 @@ __device__ void fixup_region(const RemapArgs &a, int unit, int bpb) {
     });
 }
 
-template <int PREC, int NEXT_ODD>
-__global__ void fixup_region_kernel(RemapArgs a, int bpb) {
-    pdl_enter();
-    fixup_region<PREC, NEXT_ODD>(a, blockIdx.x, bpb);
-}
-
 // Wall cell (i,j,k) all of whose wall layers are free-slip walls.
 __device__ __forceinline__ bool free_slip_cell(const LatDev &L, int i, int j, int k) {
     const bool lx = !L.px && (i == 0 || i == L.nx - 1);
@@ -822,11 +816,6 @@ __device__ void flags_region(const RemapArgs &a, int unit, int bpb) {
         }
         return -1;
     });
-}
-
-__global__ void flags_region_kernel(RemapArgs a, int bpb) {
-    pdl_enter();
-    flags_region(a, blockIdx.x, bpb);
 }
 
 // The fix-up and flags passes over the step's changed-cell list (the
