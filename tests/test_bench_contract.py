@@ -38,3 +38,18 @@ def test_l2_note_tells_resident_from_streamed_inputs():
     assert bench.l2_note(4194304 * 19 * 4).startswith("inputs larger than L2")    # 256x128x128 FP32: 319 MB
     assert bench.l2_note(4194304 * 19 * 2).startswith("inputs larger than L2")    # FP16 offsets: 159 MB
     assert bench.l2_note(32768 * 19 * 8).startswith("inputs fit in L2")           # 32^3 FP64: 5 MB
+
+
+def test_recorded_sweep_traffic_matches_its_profile():
+    """Every recorded DRAM traffic figure names a committed profile summary
+    that states the same per-launch bytes (to the summary's precision)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    for (workload, prec), rec in bench.SWEEP_TRAFFIC.items():
+        path = os.path.join(ROOT, rec["profile"])
+        assert os.path.isfile(path), rec["profile"]
+        text = open(path).read()
+        mb = rec["bytes"] / 1e6
+        shown = {f"{mb:.1f} MB", f"{mb / 1e3:.2f} GB"}
+        assert any(s in text for s in shown), (workload, prec, shown)
+        assert len(rec["src"]) == 16 and int(rec["src"], 16) >= 0
