@@ -364,9 +364,12 @@ lbm_status lbm_set_momentum_stabilisation(lbm_ctx *ctx, int enable);
 /* Choose the sweep launch shape by timing candidates on this context (runs
  * sweeps on scratch copies: the state is restored afterwards): the ring and
  * staged sweeps and the direct sweep with 128 or 256 threads, 1, 2 or 4 cells
- * per thread, fused or split, on persistent and one-tile-per-block grids.
- * The chosen shape is kept and returned through block/grid (either may be
- * NULL); lbm_get_info reports the cells per thread and the split. */
+ * per thread, fused or split, on persistent and one-tile-per-block grids,
+ * each direct-sweep shape with and without the L2 prefetch, timed for the
+ * even- and odd-step sweeps separately (the prefetch is then chosen for each
+ * parity on its own).  The chosen shape is kept and returned through
+ * block/grid (either may be NULL); lbm_get_info reports the cells per
+ * thread, the split and the prefetch mode. */
 lbm_status lbm_autotune(lbm_ctx *ctx, int *block, int *grid);
 
 /* CUDA graphs: when enabled, lbm_step replays a captured two-step graph for
